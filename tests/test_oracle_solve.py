@@ -1,0 +1,233 @@
+"""Pins of the oracle's solvers and of the discretisation as a whole.
+
+  * manufactured solutions converge at O(h^2) in L2 (P1 elements; body force derived
+    symbolically with sympy, independently of the oracle);
+  * Jacobi-PCG agrees with a sparse direct solve (scipy.sparse.linalg.spsolve);
+  * warm-start behaviour stated in the paper (Sec. 4 / 5.6, App. C): the warm start needs
+    fewer iterations, converges at the same asymptotic rate, the saving follows
+    ln(||e0_zero|| / ||e0_warm||) / R, and the relative benefit shrinks as tol tightens;
+  * Newton-Raphson: load-stepped and warm-started runs reach the same equilibrium, and
+    the local convergence is quadratic with exact inner solves.
+"""
+
+import math
+
+import numpy as np
+import pytest
+import sympy as sym
+
+import pfem_inputs as pi
+from oracle import fem, solve
+
+# --------------------------------------------------------------------------- MMS
+
+
+def _mms_body_force(dim, E, nu):
+    xs = sym.symbols("x0:%d" % dim)
+    if dim == 2:
+        u = [sym.Rational(1, 10) * sym.sin(sym.pi * xs[0]) * sym.sin(sym.pi * xs[1]),
+             sym.Rational(1, 10) * sym.sin(2 * sym.pi * xs[0]) * sym.sin(sym.pi * xs[1])]
+    else:
+        u = [sym.Rational(1, 10) * sym.sin(sym.pi * xs[0]) * sym.sin(sym.pi * xs[1]) * sym.sin(sym.pi * xs[2]),
+             sym.Rational(1, 10) * sym.sin(2 * sym.pi * xs[0]) * sym.sin(sym.pi * xs[1]) * sym.sin(sym.pi * xs[2]),
+             sym.Rational(1, 10) * sym.sin(sym.pi * xs[0]) * sym.sin(sym.pi * xs[1]) * sym.sin(2 * sym.pi * xs[2])]
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    eps = [[(sym.diff(u[i], xs[j]) + sym.diff(u[j], xs[i])) / 2 for j in range(dim)] for i in range(dim)]
+    tr = sum(eps[i][i] for i in range(dim))
+    sig = [[2 * mu * eps[i][j] + (lam * tr if i == j else 0) for j in range(dim)] for i in range(dim)]
+    f = [-sum(sym.diff(sig[i][j], xs[j]) for j in range(dim)) for i in range(dim)]
+    return sym.lambdify(xs, u, "numpy"), sym.lambdify(xs, f, "numpy")
+
+
+def _quad(dim):
+    if dim == 2:
+        a, b = 2.0 / 3.0, 1.0 / 6.0
+        lam = np.array([[a, b, b], [b, a, b], [b, b, a]])
+        return lam, np.full(3, 1.0 / 3.0)
+    a, b = 0.5854101966249685, 0.1381966011250105
+    lam = np.full((4, 4), b) + np.eye(4) * (a - b)
+    return lam, np.full(4, 0.25)
+
+
+def _eval(fn, pts):
+    vals = fn(*[pts[..., j] for j in range(pts.shape[-1])])
+    return np.stack([np.broadcast_to(v, pts.shape[:-1]) for v in vals], axis=-1)
+
+
+def _mms_error(dim, n):
+    E, nu = 1.0, 0.3
+    u_fn, f_fn = _mms_body_force(dim, E, nu)
+    if dim == 2:
+        coords, conn = pi.grid_tri(n, n)
+    else:
+        coords, conn = pi.grid_tet(n, n, n)
+    ne = conn.shape[0]
+    lo, hi = coords.min(0), coords.max(0)
+    on_b = np.any((np.abs(coords - lo) < 1e-12) | (np.abs(coords - hi) < 1e-12), axis=1)
+    mask = np.zeros(coords.shape, np.uint8)
+    mask[on_b] = 1
+    values = _eval(u_fn, coords)
+    prob = dict(dim=dim, coords=coords, conn=conn, kind="linear", mat_a=np.full(ne, E), mat_b=np.full(ne, nu),
+                dirichlet_mask=mask, dirichlet_values=values, facets=np.zeros((0, dim), np.int32),
+                traction=np.zeros((0, dim)), f_ext_extra=None, name="mms", seed=0)
+    m = fem.Mesh(prob)
+    lam, w = _quad(dim)
+    Xe = coords[conn]
+    pts = np.einsum("qa,eai->eqi", lam, Xe)
+    fq = _eval(f_fn, pts)
+    fe = np.einsum("e,q,qa,eqi->eai", m.vol, w, lam, fq)
+    fx = np.zeros(coords.shape)
+    np.add.at(fx, conn.reshape(-1), fe.reshape(-1, dim))
+    prob["f_ext_extra"] = fx
+    m = fem.Mesh(prob)
+    uh = solve.solve_linear_direct(m).reshape(-1, dim)
+    uhq = np.einsum("qa,eai->eqi", lam, uh[conn])
+    uq = _eval(u_fn, pts)
+    err = math.sqrt(float(np.einsum("e,q,eq->", m.vol, w, np.sum((uhq - uq) ** 2, axis=-1))))
+    return err
+
+
+@pytest.mark.parametrize("dim,sizes", [(2, (8, 16, 32)), (3, (4, 8, 16))])
+def test_manufactured_solution_second_order(dim, sizes):
+    errs = [_mms_error(dim, n) for n in sizes]
+    rates = [math.log(errs[i] / errs[i + 1], 2) for i in range(len(errs) - 1)]
+    assert abs(rates[-1] - 2.0) <= 0.2, (errs, rates)
+    assert all(r > 1.6 for r in rates), (errs, rates)
+
+
+# --------------------------------------------------------------------------- PCG
+
+
+def test_pcg_matches_sparse_direct_on_plate():
+    p = pi.cfg1_plate()
+    m = fem.Mesh(p)
+    u_direct = solve.solve_linear_direct(m)
+    u, it, rel_true = solve.solve_linear(m, tol=1e-13)
+    assert rel_true < 1e-12
+    assert np.linalg.norm(u - u_direct) <= 1e-10 * np.linalg.norm(u_direct)
+    assert 0 < it < 2 * 2112
+
+
+def test_pcg_skip_test_costs_no_iteration():
+    p = pi.cfg1_plate(8)
+    m = fem.Mesh(p)
+    u_direct = solve.solve_linear_direct(m)
+    u, it, _ = solve.solve_linear(m, u0=u_direct, tol=1e-8)
+    assert it == 0
+    assert np.array_equal(u, u_direct)
+
+
+@pytest.fixture(scope="module")
+def cube_runs():
+    p = pi.cube_problem(10, seed=2)
+    m = fem.Mesh(p)
+    K = fem.assemble_linear_K(m)
+    u_star = solve.solve_linear_direct(m, K=K)
+    warm = pi.make_warm_start(p, u_star, seed=20)
+    out = {"m": m, "K": K, "u_star": u_star, "u0_warm": warm}
+    for name, u0 in (("zero", None), ("warm", warm)):
+        hist = []
+        u, it, _ = solve.solve_linear(m, u0=u0, tol=1e-10, history=hist, K=K)
+        out["run_" + name] = (u, it, hist)
+    return out
+
+
+def test_warm_start_fewer_iterations_same_solution(cube_runs):
+    r = cube_runs
+    uz, kz, _ = r["run_zero"]
+    uw, kw, _ = r["run_warm"]
+    assert kw < kz
+    nrm = np.linalg.norm(r["u_star"])
+    assert np.linalg.norm(uz - r["u_star"]) <= 1e-7 * nrm
+    assert np.linalg.norm(uw - r["u_star"]) <= 1e-7 * nrm
+
+
+def _iters_to(hist, tol):
+    return next(i for i, v in enumerate(hist) if v < tol)
+
+
+def test_warm_start_same_rate_and_app_c_saving(cube_runs):
+    """Same asymptotic slope for both starts (Sec. 4.4: the rate is set by the solver, the
+    saving comes from the start) and a saving within App. C's ln(e0_zero/e0_warm)/R."""
+    r = cube_runs
+    hz = np.array(r["run_zero"][2])
+    hw = np.array(r["run_warm"][2])
+    # asymptotic rate R: mean decrease of ln(residual) per iteration between 1e-6 and 1e-10
+    def rate(h):
+        i0, i1 = _iters_to(h, 1e-6), _iters_to(h, 1e-10)
+        return (math.log(h[i0]) - math.log(h[i1])) / (i1 - i0)
+
+    Rz, Rw = rate(hz), rate(hw)
+    assert abs(Rz - Rw) <= 0.25 * Rz, (Rz, Rw)
+    m, K = r["m"], r["K"]
+    free = ~m.mask
+    def a_norm(e):
+        ef = e[free]
+        return math.sqrt(float(ef @ (K[free][:, free] @ ef)))
+
+    e0z = a_norm(fem.lifted(m, np.zeros(m.n_dofs)) - r["u_star"])
+    e0w = a_norm(fem.lifted(m, r["u0_warm"]) - r["u_star"])
+    predicted = math.log(e0z / e0w) / Rz
+    saving = _iters_to(hz, 1e-10) - _iters_to(hw, 1e-10)
+    # CG is not a stationary iteration, so App. C's difference of bounds is an upper
+    # estimate of the saving: the early superlinear phase of the zero start removes its
+    # rough error components for free, while the smooth warm-start error sits in the slow
+    # part of the spectrum.
+    assert 0 < saving <= 1.3 * predicted, (saving, predicted)
+
+
+def test_warm_start_benefit_shrinks_with_tighter_tol(cube_runs):
+    hz = cube_runs["run_zero"][2]
+    hw = cube_runs["run_warm"][2]
+    ratios = [_iters_to(hz, t) / max(1, _iters_to(hw, t)) for t in (1e-3, 1e-6, 1e-10)]
+    assert ratios[0] > ratios[1] > ratios[2] > 1.0, ratios
+
+
+# --------------------------------------------------------------------------- Newton
+
+
+@pytest.fixture(scope="module")
+def nh_bar():
+    p = pi.bar_problem(8, 2, 2, seed=3, stretch=0.2, length=4.0)
+    return p, fem.Mesh(p)
+
+
+def test_newton_load_steps_and_warm_start_agree(nh_bar):
+    p, m = nh_bar
+    u5, n5, _ = solve.solve_newton(m, tol=1e-10, n_load_steps=5, inner_tol=1e-12)
+    assert np.linalg.norm(fem.residual(m, u5)) <= 1e-9 * solve.newton_reference(m, 1.0)
+    warm = pi.make_warm_start(p, u5, seed=30)
+    uw, nw, _ = solve.solve_newton(m, u0=warm, tol=1e-10, n_load_steps=1, inner_tol=1e-12)
+    assert np.linalg.norm(uw - u5) <= 1e-8 * np.linalg.norm(u5)
+    assert nw < n5
+    u1, n1, _ = solve.solve_newton(m, tol=1e-10, n_load_steps=1, inner_tol=1e-12)
+    assert np.linalg.norm(u1 - u5) <= 1e-8 * np.linalg.norm(u5)
+    assert nw < n1
+
+
+def test_newton_quadratic_convergence(nh_bar):
+    p, m = nh_bar
+    log = []
+    solve.solve_newton(m, tol=1e-13, n_load_steps=1, direct=True, log=log)
+    rel = [x[2] for x in log]
+    # once in the basin (rel < 1e-2) each step at least squares the residual up to a constant
+    pairs = [(a, b) for a, b in zip(rel[:-1], rel[1:]) if a < 1e-2 and b > 1e-14]
+    assert pairs, rel
+    for a, b in pairs:
+        assert b <= 50.0 * a * a, rel
+
+
+def test_newton_small_load_matches_linear_solution():
+    """For a tiny prescribed stretch the Neo-Hookean equilibrium tends to the linear one
+    with the same Lame parameters (difference is second order in the load)."""
+    p = pi.bar_problem(6, 2, 2, seed=5, stretch=1e-4, length=3.0)
+    m_nh = fem.Mesh(p)
+    mu, lam = p["mat_a"], p["mat_b"]
+    q = dict(p)
+    q["kind"] = "linear"
+    q["mat_a"] = mu * (3 * lam + 2 * mu) / (lam + mu)
+    q["mat_b"] = lam / (2 * (lam + mu))
+    u_lin = solve.solve_linear_direct(fem.Mesh(q))
+    u_nh, _, _ = solve.solve_newton(m_nh, tol=1e-12, direct=True)
+    assert np.linalg.norm(u_nh - u_lin) <= 1e-3 * np.linalg.norm(u_lin)
