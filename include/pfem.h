@@ -1,0 +1,181 @@
+/*
+ * pfem.h - C ABI of the GB300 P1 finite-element operator and its warm-started solvers.
+ *
+ * The library evaluates, matrix-free and element by element, the discrete energy, the
+ * internal-force residual and the tangent-times-vector product of P1 triangles (plane
+ * strain) and P1 tetrahedra for linear elasticity and compressible Neo-Hookean material,
+ * and drives Jacobi-PCG and Newton-Krylov solves started from a caller-supplied guess.
+ *
+ * Paper: "Pretrained Finite Element Method" (PFEM, arXiv 2601.03086).
+ *   - energy loss, linear:       Sec. 3.1, Eq. of the plate loss (Psi = 1/2 sigma:eps)
+ *   - energy loss, Neo-Hookean:  Sec. 3.2 (Psi = 1/2 lam ln^2 J - mu ln J + 1/2 mu (I1 - d))
+ *   - explicit FE derivatives:   App. A (shape-function differentiation)
+ *   - f_int, f_ext, tangent:     App. B (principle of virtual power, total Lagrangian,
+ *                                K = K_geo + K_mat, Newton-Raphson with load steps)
+ *   - warm start + criterion:    Sec. 2.3.2 (U^(0) = U^NO, ||r|| < tol, skip test)
+ *
+ * Conventions shared by every entry point
+ *   - Node vectors (u, v, y, r, ...) are device pointers, DOF-interleaved: entry
+ *     node*dim + i. Their element type is float for PFEM_F32 and double for PFEM_F64.
+ *     The caller owns them; the library never frees or retains them.
+ *   - Every call is ordered on the stream given at pfem_mesh_create (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream). Calls returning host values
+ *     synchronise that stream; the others only enqueue work.
+ *   - Dirichlet DOFs (mask = 1) are eliminated: the linear operator on full-length vectors
+ *     is A = P K P + (I - P), P = projector on free DOFs; residuals are zero there.
+ *   - No call traps the GPU. Errors come back as pfem_status; pfem_last_error() returns a
+ *     thread-local message for the last failure of the calling thread.
+ *   - Results are bitwise reproducible run to run (fixed reduction orders, no float
+ *     atomics) for the same mesh, inputs and device.
+ */
+#ifndef PFEM_H
+#define PFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PFEM_OK = 0,
+  PFEM_ERR_INVALID_ARG = 1,        /* bad pointer, size, index, material or option */
+  PFEM_ERR_DEGENERATE_ELEMENT = 2, /* |det D| <= 1e-12 (max edge)^d in the reference mesh */
+  PFEM_ERR_INVERTED = 3,           /* some element has J = det F <= 0 (Neo-Hookean) */
+  PFEM_ERR_NONFINITE = 4,          /* NaN/Inf met in a reduction */
+  PFEM_ERR_NOT_CONVERGED = 5,      /* iteration cap reached */
+  PFEM_ERR_OUT_OF_MEMORY = 6,      /* device or host allocation failed */
+  PFEM_ERR_OVER_BUDGET = 7,        /* request can never fit the server's HBM budget */
+  PFEM_PENDING = 8,                /* serving: result not ready yet */
+  PFEM_ERR_TIMEOUT = 9,            /* a bounded wait gave up */
+  PFEM_ERR_CUDA = 10,              /* a CUDA runtime call failed (message has details) */
+  PFEM_ERR_UNSUPPORTED = 11        /* combination not built (e.g. dim or dtype) */
+} pfem_status;
+
+typedef enum { PFEM_LINEAR = 0, PFEM_NEOHOOKEAN = 1 } pfem_material_kind;
+typedef enum { PFEM_F32 = 0, PFEM_F64 = 1 } pfem_dtype;
+
+typedef struct pfem_mesh_s* pfem_mesh_t;
+
+/* Problem description (Sec. 2.3.1 point-cloud inputs: geometry, material, boundary
+ * conditions). All pointers are HOST pointers, read during pfem_mesh_create only. */
+typedef struct {
+  int32_t dim;                     /* 2: P1 triangles, plane strain, unit thickness; 3: P1 tets */
+  int64_t n_nodes;                 /* >= 1 */
+  const double* coords;            /* n_nodes*dim reference coordinates X, node-major */
+  int64_t n_elems;                 /* >= 0 */
+  const int32_t* conn;             /* n_elems*(dim+1) node ids; either orientation accepted */
+  int32_t kind;                    /* pfem_material_kind */
+  const double* mat_a;             /* per element: E (linear, > 0) | mu (Neo-Hookean, > 0) */
+  const double* mat_b;             /* per element: nu in (-1, 0.5) (linear) | lambda >= 0 (NH) */
+  const uint8_t* dirichlet_mask;   /* n_nodes*dim, 1 = prescribed DOF; NULL = none */
+  const double* dirichlet_values;  /* n_nodes*dim values at full load; NULL = all zero */
+  int64_t n_facets;                /* traction facets (edges in 2-D, triangles in 3-D) */
+  const int32_t* facets;           /* n_facets*dim node ids */
+  const double* traction;          /* n_facets*dim constant traction per facet */
+  const double* f_ext_extra;       /* n_nodes*dim extra nodal force (body force), may be NULL */
+} pfem_mesh_desc;
+
+/* Plan statistics of a mesh (host-side bookkeeping; useful for traffic accounting). */
+typedef struct {
+  int64_t n_nodes, n_elems, n_dofs, n_free_dofs;
+  int64_t n_tiles;          /* element tiles (shared-memory work units) */
+  int64_t n_local_nodes;    /* sum over tiles of nodes touched by the tile */
+  int64_t n_halo_nodes;     /* nodes whose elements span more than one tile */
+  int64_t n_partials;       /* (tile, halo node) pairs */
+  int64_t device_bytes;     /* device memory held by the mesh */
+  int32_t max_tile_elems, max_tile_nodes;
+} pfem_mesh_stats;
+
+typedef struct {
+  int32_t iterations;              /* PCG iterations (all inner PCG iterations for Newton) */
+  int32_t newton_iterations;       /* tangent solves (Newton only) */
+  int32_t replacements;            /* FP64 residual replacements performed */
+  int32_t inverted_backtracks;     /* Newton step halvings caused by J <= 0 */
+  double rel_residual_recursive;   /* ||r_k|| / ref as tracked by the iteration */
+  double rel_residual_true_f64;    /* ||P(f_ext - f_int(u))|| / ref with the FP64 operator */
+  double initial_rel_residual;     /* ||r(u0)|| / ref, the Sec. 2.3.2 skip-test quantity */
+  double reference_norm;           /* ref = ||r(u_lift)||: zero free DOFs, prescribed values */
+  pfem_status status;
+} pfem_solve_info;
+
+/* ---- mesh ------------------------------------------------------------------------ */
+
+/* Validate, plan (Morton-ordered element tiles, tile-local node lists, halo lists) and
+ * upload a mesh. The library owns the resulting device memory until pfem_mesh_destroy.
+ * Errors: INVALID_ARG (sizes, ids, materials, non-finite input), DEGENERATE_ELEMENT,
+ * OUT_OF_MEMORY, CUDA. On error *out is NULL. */
+pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem_mesh_t* out);
+void pfem_mesh_destroy(pfem_mesh_t mesh);
+
+/* Host-only: validate and plan desc exactly as pfem_mesh_create does, then check the plan's
+ * structural invariants (every element in one tile, every incidence in one slot, complete
+ * nodes holding all their incidences, halo nodes with one partial per touching tile).
+ * Touches no device; fills *out (may be NULL). Same error codes as pfem_mesh_create. */
+pfem_status pfem_plan_check(const pfem_mesh_desc* desc, pfem_mesh_stats* out);
+pfem_status pfem_mesh_stats_get(pfem_mesh_t mesh, pfem_mesh_stats* out);
+
+/* Load step factor s (App. B load stepping): f_ext and the prescribed values are both
+ * multiplied by s in every later call. Default 1. */
+pfem_status pfem_mesh_set_load_scale(pfem_mesh_t mesh, double s);
+
+/* ---- element operator (Sec. 3.1/3.2 energies; App. B forces and tangent) ----------- */
+
+/* Pi(u) = sum_e V_e Psi_e(u) - s f_ext . u and the strain part sum_e V_e Psi_e(u).
+ * u: n_dofs device vector (dtype). Results are written to HOST doubles (either may be
+ * NULL); the call synchronises. Neo-Hookean elements with J <= 0 make both +inf and the
+ * call returns PFEM_ERR_INVERTED. Arithmetic: element terms in dtype, sums in FP64. */
+pfem_status pfem_energy(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, double* energy,
+                        double* strain_energy);
+
+/* r = P (f_int(u) - s f_ext): the gradient of Pi on free DOFs, zero on Dirichlet DOFs
+ * (App. B: f_iI = int dN_I/dX_l F_ik S_kl dV; linear: f_int = K u). u, r: n_dofs device
+ * vectors of dtype, r written. Asynchronous. */
+pfem_status pfem_residual(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, void* r);
+
+/* y = A(u) v = P K(u) P v + (I - P) v, K(u) = K_geo + K_mat (App. B); u is ignored for
+ * linear material (may be NULL). Asynchronous. */
+pfem_status pfem_tangent_apply(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, const void* v,
+                               void* y);
+
+/* d = diag A(u): diag K(u) on free DOFs, 1 on Dirichlet DOFs (the Jacobi preconditioner).
+ * u ignored for linear material. Asynchronous. */
+pfem_status pfem_jacobi_diag(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, void* d);
+
+/* ---- warm-started solvers (Sec. 2.3.2; App. B) ------------------------------------- */
+
+/* Linear elasticity K U = F by Jacobi-PCG started from u0 (NULL = zero). The prescribed
+ * values overwrite u0 on Dirichlet DOFs. Stops when ||r_k|| / ref < tol with
+ * ref = ||r(u_lift)|| (= ||f_ext,free|| when the prescribed values are zero); checked
+ * before the first iteration (skip test). dtype selects the element arithmetic (F32: FP32
+ * operator with FP64 vectors, dots and norms plus FP64 residual replacement; F64: FP64
+ * throughout). u0, u_out: FP64 device vectors (may alias). info may be NULL.
+ * Returns NOT_CONVERGED if max_iter is reached (u_out then holds the last iterate). */
+pfem_status pfem_solve_linear(pfem_mesh_t mesh, pfem_dtype dtype, const double* u0, double tol,
+                              int32_t max_iter, double* u_out, pfem_solve_info* info);
+
+/* Neo-Hookean (or linear) equilibrium by Newton-Raphson with n_load_steps equal load steps
+ * (App. B); a warm start passes u0 = U^NO and n_load_steps = 1, bypassing the earlier
+ * steps. Residuals and updates in FP64; tangent applies in dtype; inner Jacobi-PCG to
+ * inner_tol relative to the current residual. Step halving (<= 10) when a trial makes
+ * J <= 0, else INVERTED. u0/u_out: FP64 device vectors (may alias, u0 NULL = zero). */
+pfem_status pfem_solve_newton(pfem_mesh_t mesh, pfem_dtype dtype, const double* u0, double tol,
+                              int32_t n_load_steps, int32_t max_newton, double inner_tol,
+                              double* u_out, pfem_solve_info* info);
+
+/* Solver loop style for later solves (process-wide): 0 (default) runs the PCG iteration
+ * as a CUDA graph with a device-side while loop; 1 launches it one iteration at a time with
+ * a host-synchronised convergence check (the plain GPU loop used as the serving baseline). */
+pfem_status pfem_set_solver_mode(int32_t mode);
+
+/* ---- misc ------------------------------------------------------------------------- */
+
+const char* pfem_last_error(void);
+/* Library version string. */
+const char* pfem_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFEM_H */

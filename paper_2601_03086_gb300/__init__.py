@@ -1,0 +1,22 @@
+"""GB300 (sm_103a) matrix-free P1 finite-element operator and warm-started solvers (PFEM).
+
+The compute path is libpfem.so (hand-written CUDA, built in-tree by build.py); this package
+is the Python binding of its C ABI. Importing it does not load the library; the first call
+does, and raises if the library has not been built.
+"""
+
+from .api import (  # noqa: F401
+    Mesh,
+    pfem_energy,
+    pfem_jacobi_diag,
+    pfem_mesh_create,
+    pfem_mesh_destroy,
+    pfem_mesh_set_load_scale,
+    pfem_plan_check,
+    pfem_residual,
+    pfem_set_solver_mode,
+    pfem_solve_linear,
+    pfem_solve_newton,
+    pfem_tangent_apply,
+    pfem_version,
+)

@@ -1,0 +1,125 @@
+"""ctypes declarations of the C ABI in include/pfem.h (argument marshalling only)."""
+
+import ctypes as C
+import os
+
+_DIR = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_DIR, "libpfem.so")
+
+PFEM_OK = 0
+STATUS = {
+    0: "PFEM_OK",
+    1: "PFEM_ERR_INVALID_ARG",
+    2: "PFEM_ERR_DEGENERATE_ELEMENT",
+    3: "PFEM_ERR_INVERTED",
+    4: "PFEM_ERR_NONFINITE",
+    5: "PFEM_ERR_NOT_CONVERGED",
+    6: "PFEM_ERR_OUT_OF_MEMORY",
+    7: "PFEM_ERR_OVER_BUDGET",
+    8: "PFEM_PENDING",
+    9: "PFEM_ERR_TIMEOUT",
+    10: "PFEM_ERR_CUDA",
+    11: "PFEM_ERR_UNSUPPORTED",
+}
+PFEM_LINEAR, PFEM_NEOHOOKEAN = 0, 1
+PFEM_F32, PFEM_F64 = 0, 1
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int32),
+        ("n_nodes", C.c_int64),
+        ("coords", C.c_void_p),
+        ("n_elems", C.c_int64),
+        ("conn", C.c_void_p),
+        ("kind", C.c_int32),
+        ("mat_a", C.c_void_p),
+        ("mat_b", C.c_void_p),
+        ("dirichlet_mask", C.c_void_p),
+        ("dirichlet_values", C.c_void_p),
+        ("n_facets", C.c_int64),
+        ("facets", C.c_void_p),
+        ("traction", C.c_void_p),
+        ("f_ext_extra", C.c_void_p),
+    ]
+
+
+class MeshStats(C.Structure):
+    _fields_ = [
+        ("n_nodes", C.c_int64),
+        ("n_elems", C.c_int64),
+        ("n_dofs", C.c_int64),
+        ("n_free_dofs", C.c_int64),
+        ("n_tiles", C.c_int64),
+        ("n_local_nodes", C.c_int64),
+        ("n_halo_nodes", C.c_int64),
+        ("n_partials", C.c_int64),
+        ("device_bytes", C.c_int64),
+        ("max_tile_elems", C.c_int32),
+        ("max_tile_nodes", C.c_int32),
+    ]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [
+        ("iterations", C.c_int32),
+        ("newton_iterations", C.c_int32),
+        ("replacements", C.c_int32),
+        ("inverted_backtracks", C.c_int32),
+        ("rel_residual_recursive", C.c_double),
+        ("rel_residual_true_f64", C.c_double),
+        ("initial_rel_residual", C.c_double),
+        ("reference_norm", C.c_double),
+        ("status", C.c_int32),
+    ]
+
+
+# name -> (restype, argtypes); every entry must be exported by libpfem.so
+SIGNATURES = {
+    "pfem_mesh_create": (C.c_int32, [C.POINTER(MeshDesc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "pfem_mesh_destroy": (None, [C.c_void_p]),
+    "pfem_plan_check": (C.c_int32, [C.POINTER(MeshDesc), C.POINTER(MeshStats)]),
+    "pfem_mesh_stats_get": (C.c_int32, [C.c_void_p, C.POINTER(MeshStats)]),
+    "pfem_mesh_set_load_scale": (C.c_int32, [C.c_void_p, C.c_double]),
+    "pfem_energy": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "pfem_residual": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pfem_tangent_apply": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pfem_jacobi_diag": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pfem_solve_linear": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
+                                      C.POINTER(SolveInfo)]),
+    "pfem_solve_newton": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_int32,
+                                      C.c_double, C.c_void_p, C.POINTER(SolveInfo)]),
+    "pfem_set_solver_mode": (C.c_int32, [C.c_int32]),
+    "pfem_last_error": (C.c_char_p, []),
+    "pfem_version": (C.c_char_p, []),
+}
+
+_LIB = None
+
+
+class PfemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+def lib():
+    """Load libpfem.so (raises if it has not been built: there is no fallback path)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpfem.so is not built; run paper_2601_03086_gb300.build.build() first")
+        h = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(h, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = h
+    return _LIB
+
+
+def check(status):
+    if status != PFEM_OK:
+        msg = lib().pfem_last_error()
+        raise PfemError(status, msg.decode() if msg else "")
+    return status

@@ -1,0 +1,315 @@
+// C ABI: mesh lifetime and the element-operator entry points (see include/pfem.h).
+
+#include <cstring>
+#include <new>
+
+#include "kernels_vec.cuh"
+#include "pfem_internal.h"
+#include "solver.h"
+
+namespace pfem {
+const char* last_error_cstr();
+
+namespace {
+
+struct ArenaBuilder {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off = (off + bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+template <typename T>
+pfem_status upload(void* base, size_t off, const std::vector<T>& v, cudaStream_t s) {
+  if (v.empty()) return PFEM_OK;
+  PFEM_CUDA(cudaMemcpyAsync(static_cast<char*>(base) + off, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return PFEM_OK;
+}
+
+}  // namespace
+
+pfem_status check_mesh(pfem_mesh_t m) {
+  if (!m) {
+    set_error("null mesh");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  return PFEM_OK;
+}
+
+}  // namespace pfem
+
+using namespace pfem;
+
+extern "C" {
+
+const char* pfem_last_error(void) { return last_error_cstr(); }
+const char* pfem_version(void) { return "pfem-gb300 0.1 (sm_103a)"; }
+
+pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem_mesh_t* out) {
+  if (!out) {
+    set_error("out is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  *out = nullptr;
+  HostPlan hp;
+  std::vector<double> fext;
+  pfem_status st = build_plan(desc, &hp, &fext);
+  if (st != PFEM_OK) return st;
+  const int dim = hp.dim;
+  const int64_t nd = hp.n_nodes * dim;
+  std::vector<float> fext_f(fext.size());
+  for (size_t i = 0; i < fext.size(); ++i) fext_f[i] = (float)fext[i];
+  std::vector<double> vals((size_t)nd, 0.0);
+  std::vector<uint8_t> mask((size_t)nd, 0);
+  int64_t n_free = nd;
+  for (int64_t i = 0; i < nd; ++i) {
+    if (desc->dirichlet_mask && desc->dirichlet_mask[i]) {
+      mask[(size_t)i] = 1;
+      --n_free;
+      if (desc->dirichlet_values) vals[(size_t)i] = desc->dirichlet_values[i];
+    }
+  }
+
+  ArenaBuilder ab;
+  const int64_t nt = hp.n_tiles();
+  const size_t o_ta = ab.take(hp.tile_a.size() * 4);
+  const size_t o_tb = ab.take(hp.tile_b.size() * 4);
+  const size_t o_lf = ab.take(hp.lnode_f.size() * 4);
+  const size_t o_ld = ab.take(hp.lnode_d.size() * 8);
+  const size_t o_so = ab.take(hp.slot_off.size() * 2 + 2);
+  const size_t o_ec = ab.take(hp.ecode.size() * 2);
+  const size_t o_mf = ab.take(hp.emat_f.size() * 4);
+  const size_t o_md = ab.take(hp.emat_d.size() * 8);
+  const size_t o_hi = ab.take(hp.halo_info.size() * 4);
+  const size_t o_hp = ab.take(hp.halo_ptr.size() * 4);
+  const size_t o_hs = ab.take(hp.halo_src.size() * 4);
+  const size_t o_pa = ab.take((size_t)std::max<int64_t>(hp.n_partials, 1) * dim * sizeof(double) * 2);
+  const size_t o_te = ab.take((size_t)std::max<int64_t>(nt, 1) * sizeof(double));
+  const size_t o_inv = ab.take(16);
+  const size_t o_fe = ab.take((size_t)nd * 8);
+  const size_t o_ff = ab.take((size_t)nd * 4);
+  const size_t o_dv = ab.take((size_t)nd * 8);
+  const size_t o_dm = ab.take((size_t)nd);
+  const size_t o_rp = ab.take((size_t)kReduceBlocks * 4 * sizeof(double));
+  const size_t o_rc = ab.take(64);
+  const size_t o_ro = ab.take(8 * sizeof(double));
+
+  pfem_mesh_s* m = new (std::nothrow) pfem_mesh_s();
+  if (!m) {
+    set_error("host allocation failed");
+    return PFEM_ERR_OUT_OF_MEMORY;
+  }
+  m->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaGetDevice(&m->device);
+  cudaError_t ce = cudaMalloc(&m->arena, ab.off);
+  if (ce != cudaSuccess) {
+    delete m;
+    return cuda_fail(ce, "cudaMalloc(mesh arena)");
+  }
+  m->arena_bytes = ab.off;
+  ce = cudaMallocHost(&m->host_out, 8 * sizeof(double) + 4 * sizeof(int32_t));
+  if (ce != cudaSuccess) {
+    cudaFree(m->arena);
+    delete m;
+    return cuda_fail(ce, "cudaMallocHost");
+  }
+  m->host_int = reinterpret_cast<int32_t*>(m->host_out + 8);
+  char* base = static_cast<char*>(m->arena);
+  cudaStream_t s = m->stream;
+  auto fail = [&](pfem_status e) {
+    cudaStreamSynchronize(s);
+    cudaFree(m->arena);
+    cudaFreeHost(m->host_out);
+    delete m;
+    return e;
+  };
+  if ((st = upload(base, o_ta, hp.tile_a, s)) || (st = upload(base, o_tb, hp.tile_b, s)) ||
+      (st = upload(base, o_lf, hp.lnode_f, s)) || (st = upload(base, o_ld, hp.lnode_d, s)) ||
+      (st = upload(base, o_so, hp.slot_off, s)) || (st = upload(base, o_ec, hp.ecode, s)) ||
+      (st = upload(base, o_mf, hp.emat_f, s)) || (st = upload(base, o_md, hp.emat_d, s)) ||
+      (st = upload(base, o_hi, hp.halo_info, s)) || (st = upload(base, o_hp, hp.halo_ptr, s)) ||
+      (st = upload(base, o_hs, hp.halo_src, s)) || (st = upload(base, o_fe, fext, s)) ||
+      (st = upload(base, o_ff, fext_f, s)) || (st = upload(base, o_dv, vals, s)) || (st = upload(base, o_dm, mask, s)))
+    return fail(st);
+  ce = cudaMemsetAsync(base + o_inv, 0, 16, s);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(base + o_rc, 0, 64, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);  // host vectors die at return
+  if (ce != cudaSuccess) return fail(cuda_fail(ce, "mesh upload"));
+
+  DevPlan& P = m->plan;
+  P.dim = dim;
+  P.kind = desc->kind;
+  P.n_tiles = (int)nt;
+  P.n_halo = (int)hp.n_halo();
+  P.max_local = hp.max_local;
+  P.slot_cap = hp.max_elems * hp.nv;
+  P.n_nodes = hp.n_nodes;
+  P.n_partials = hp.n_partials;
+  P.tile_a = reinterpret_cast<const int4*>(base + o_ta);
+  P.tile_b = reinterpret_cast<const int4*>(base + o_tb);
+  P.lnode_f = reinterpret_cast<const float4*>(base + o_lf);
+  P.lnode_d = reinterpret_cast<const PfemDouble4*>(base + o_ld);
+  P.slot_off = reinterpret_cast<const uint16_t*>(base + o_so);
+  P.ecode = reinterpret_cast<const ushort4*>(base + o_ec);
+  P.emat_f = reinterpret_cast<const float2*>(base + o_mf);
+  P.emat_d = reinterpret_cast<const double2*>(base + o_md);
+  P.halo_info = reinterpret_cast<const int32_t*>(base + o_hi);
+  P.halo_ptr = reinterpret_cast<const int32_t*>(base + o_hp);
+  P.halo_src = reinterpret_cast<const int32_t*>(base + o_hs);
+  P.partial = base + o_pa;
+  P.tile_energy = reinterpret_cast<double*>(base + o_te);
+  P.inverted = reinterpret_cast<int32_t*>(base + o_inv);
+  P.f_ext = reinterpret_cast<const double*>(base + o_fe);
+  P.f_ext_f = reinterpret_cast<const float*>(base + o_ff);
+  P.dvalues = reinterpret_cast<const double*>(base + o_dv);
+  P.dmask = reinterpret_cast<const uint8_t*>(base + o_dm);
+  m->red_partials = reinterpret_cast<double*>(base + o_rp);
+  m->red_counter = reinterpret_cast<unsigned int*>(base + o_rc);
+  m->red_out = reinterpret_cast<double*>(base + o_ro);
+  m->n_dofs = nd;
+  m->n_free = n_free;
+
+  pfem_mesh_stats& S = m->stats;
+  S.n_nodes = hp.n_nodes;
+  S.n_elems = hp.n_elems;
+  S.n_dofs = nd;
+  S.n_free_dofs = n_free;
+  S.n_tiles = nt;
+  S.n_local_nodes = hp.n_local();
+  S.n_halo_nodes = hp.n_halo();
+  S.n_partials = hp.n_partials;
+  S.device_bytes = (int64_t)ab.off;
+  S.max_tile_elems = hp.max_elems;
+  S.max_tile_nodes = hp.max_local;
+  *out = m;
+  return PFEM_OK;
+}
+
+pfem_status pfem_plan_check(const pfem_mesh_desc* desc, pfem_mesh_stats* out) {
+  HostPlan hp;
+  std::vector<double> fext;
+  pfem_status st = build_plan(desc, &hp, &fext);
+  if (st != PFEM_OK) return st;
+  if ((st = verify_plan(desc, hp)) != PFEM_OK) return st;
+  if (out) {
+    std::memset(out, 0, sizeof(*out));
+    out->n_nodes = hp.n_nodes;
+    out->n_elems = hp.n_elems;
+    out->n_dofs = hp.n_nodes * hp.dim;
+    int64_t nf = out->n_dofs;
+    if (desc->dirichlet_mask)
+      for (int64_t i = 0; i < out->n_dofs; ++i) nf -= desc->dirichlet_mask[i] ? 1 : 0;
+    out->n_free_dofs = nf;
+    out->n_tiles = hp.n_tiles();
+    out->n_local_nodes = hp.n_local();
+    out->n_halo_nodes = hp.n_halo();
+    out->n_partials = hp.n_partials;
+    out->max_tile_elems = hp.max_elems;
+    out->max_tile_nodes = hp.max_local;
+  }
+  return PFEM_OK;
+}
+
+void pfem_mesh_destroy(pfem_mesh_t m) {
+  if (!m) return;
+  cudaStreamSynchronize(m->stream);
+  solver_release(m);
+  cudaFree(m->arena);
+  cudaFreeHost(m->host_out);
+  delete m;
+}
+
+pfem_status pfem_mesh_stats_get(pfem_mesh_t m, pfem_mesh_stats* out) {
+  pfem_status st = check_mesh(m);
+  if (st) return st;
+  if (!out) {
+    set_error("out is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  *out = m->stats;
+  out->device_bytes += (int64_t)solver_bytes(m);
+  return PFEM_OK;
+}
+
+pfem_status pfem_mesh_set_load_scale(pfem_mesh_t m, double s) {
+  pfem_status st = check_mesh(m);
+  if (st) return st;
+  if (!std::isfinite(s)) {
+    set_error("non-finite load scale");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  m->load_scale = s;
+  return PFEM_OK;
+}
+
+static pfem_status op_common(pfem_mesh_t m, pfem_dtype dt) {
+  pfem_status st = check_mesh(m);
+  if (st) return st;
+  if (dt != PFEM_F32 && dt != PFEM_F64) {
+    set_error("unknown dtype %d", (int)dt);
+    return PFEM_ERR_INVALID_ARG;
+  }
+  return PFEM_OK;
+}
+
+pfem_status pfem_energy(pfem_mesh_t m, pfem_dtype dt, const void* u, double* energy, double* strain_energy) {
+  pfem_status st = op_common(m, dt);
+  if (st) return st;
+  if (!u) {
+    set_error("u is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  OpArgs a{u, nullptr, nullptr, nullptr, nullptr, m->load_scale};
+  PFEM_CUDA(cudaMemsetAsync(m->plan.inverted, 0, sizeof(int32_t), m->stream));
+  if ((st = launch_element_op(m->plan, OP_ENERGY, dt, dt, a, m->stream))) return st;
+  if ((st = launch_energy_finalize(m->plan, dt, u, m->load_scale, m->red_partials, m->red_counter, m->red_out,
+                                   m->stream)))
+    return st;
+  PFEM_CUDA(cudaMemcpyAsync(m->host_out, m->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
+  PFEM_CUDA(cudaMemcpyAsync(m->host_int, m->plan.inverted, sizeof(int32_t), cudaMemcpyDeviceToHost, m->stream));
+  PFEM_CUDA(cudaStreamSynchronize(m->stream));
+  if (energy) *energy = m->host_out[0];
+  if (strain_energy) *strain_energy = m->host_out[1];
+  if (m->host_int[0] > 0) {
+    set_error("%d element(s) with J <= 0", m->host_int[0]);
+    return PFEM_ERR_INVERTED;
+  }
+  return PFEM_OK;
+}
+
+pfem_status pfem_residual(pfem_mesh_t m, pfem_dtype dt, const void* u, void* r) {
+  pfem_status st = op_common(m, dt);
+  if (st) return st;
+  if (!u || !r) {
+    set_error("u/r is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  OpArgs a{u, nullptr, nullptr, r, nullptr, m->load_scale};
+  return launch_element_op(m->plan, OP_RESIDUAL, dt, dt, a, m->stream);
+}
+
+pfem_status pfem_tangent_apply(pfem_mesh_t m, pfem_dtype dt, const void* u, const void* v, void* y) {
+  pfem_status st = op_common(m, dt);
+  if (st) return st;
+  if (!v || !y || (m->plan.kind == PFEM_NEOHOOKEAN && !u)) {
+    set_error("u/v/y is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  OpArgs a{u, v, y, nullptr, nullptr, m->load_scale};
+  return launch_element_op(m->plan, OP_TANGENT, dt, dt, a, m->stream);
+}
+
+pfem_status pfem_jacobi_diag(pfem_mesh_t m, pfem_dtype dt, const void* u, void* d) {
+  pfem_status st = op_common(m, dt);
+  if (st) return st;
+  if (!d || (m->plan.kind == PFEM_NEOHOOKEAN && !u)) {
+    set_error("u/d is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  OpArgs a{u, nullptr, nullptr, nullptr, d, m->load_scale};
+  return launch_element_op(m->plan, OP_DIAG, dt, dt, a, m->stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,169 @@
+// Internal declarations shared by the translation units of libpfem.
+//
+// Data layout (device, per mesh)
+//   Elements are reordered along a Morton curve of their centroids and cut into tiles of at
+//   most kTileElems elements touching at most kTileNodes distinct nodes. A tile is the unit
+//   of work of one CTA: its nodes are staged in shared memory, every element of the tile is
+//   evaluated once, its corner contributions land in per-incidence shared-memory slots, and
+//   each tile node sums its slots in a fixed order (ascending element position, so the sum
+//   is bitwise reproducible without float atomics).
+//   A node whose incident elements all lie in one tile ("complete") is written directly by
+//   that tile. A node shared by several tiles ("halo") gets one partial per tile, written to
+//   a scratch buffer; a second pass sums each halo node's partials in ascending tile order.
+//
+//   tile_a[t]  = {elem_begin, n_elem, lnode_begin, n_local}
+//   tile_b[t]  = {n_complete, partial_begin, 0, 0}
+//   lnode_f[l] = {x - x_anchor, y - y_anchor, z - z_anchor, info}  (float4; info bits below)
+//   lnode_d[l] = same coordinates in double (for the FP64 instantiation)
+//   slot_off[l]= first incidence slot of the tile node (uint16; the tile's slots run
+//                [0, n_elem*nv); a node's in-tile degree is slot_off[l+1]-slot_off[l], the
+//                last node's end is n_elem*nv)
+//   ecode[e]   = 4 x uint16 per element: local node index (bits 0-9) | rank (bits 10-15),
+//                rank = position of this incidence among the node's incidences in the tile
+//   emat_f/d[e]= (mu, lambda) per element (linear (E, nu) converted on the host)
+//   info       = node id (bits 0-27) | Dirichlet mask of DOF i at bit 28+i
+//   halo_info[h], halo_ptr[h..h+1], halo_src[k]: halo nodes (sorted by id) and the indices
+//                of their partials in ascending tile order
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pfem.h"
+
+namespace pfem {
+
+struct __align__(32) PfemDouble4 {
+  double x, y, z, w;
+};
+
+constexpr int kTileElems = 1024;   // max elements per tile
+constexpr int kTileNodes = 1024;   // max distinct nodes per tile (10-bit local index)
+constexpr int kMaxRank = 63;       // max incidences of one node inside one tile (6 bits)
+constexpr int kInfoIdBits = 28;
+constexpr uint32_t kInfoIdMask = (1u << kInfoIdBits) - 1u;
+constexpr int kThreads = 256;      // threads per tile CTA
+constexpr int kReduceBlocks = 296; // fixed grid of the deterministic FP64 reductions (2 x 148)
+
+void set_error(const char* fmt, ...);
+pfem_status cuda_fail(cudaError_t e, const char* what);
+
+#define PFEM_CUDA(call)                                         \
+  do {                                                          \
+    cudaError_t _e = (call);                                    \
+    if (_e != cudaSuccess) return ::pfem::cuda_fail(_e, #call); \
+  } while (0)
+
+// Host-side tile plan (built by plan.cpp).
+struct HostPlan {
+  int dim = 3, nv = 4;
+  int64_t n_nodes = 0, n_elems = 0;
+  int max_local = 0, max_elems = 0;
+  std::vector<int32_t> tile_a;    // 4 per tile
+  std::vector<int32_t> tile_b;    // 4 per tile
+  std::vector<float> lnode_f;     // 4 per local node
+  std::vector<double> lnode_d;    // 4 per local node
+  std::vector<uint16_t> slot_off; // 1 per local node
+  std::vector<uint16_t> ecode;    // 4 per element
+  std::vector<float> emat_f;      // 2 per element
+  std::vector<double> emat_d;     // 2 per element
+  std::vector<int32_t> halo_info; // 1 per halo node
+  std::vector<int32_t> halo_ptr;  // n_halo + 1
+  std::vector<int32_t> halo_src;  // n_partials
+  int64_t n_partials = 0;
+  std::vector<int32_t> elem_perm; // original element id at each tile-order position
+  int64_t n_tiles() const { return (int64_t)tile_a.size() / 4; }
+  int64_t n_local() const { return (int64_t)slot_off.size(); }
+  int64_t n_halo() const { return (int64_t)halo_info.size(); }
+};
+
+// Validates desc and builds the plan plus the FP64 external force. Returns status.
+pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* plan, std::vector<double>* f_ext,
+                       int tile_elems = kTileElems);
+
+// Structural self-check of a plan against its description (host only).
+pfem_status verify_plan(const pfem_mesh_desc* d, const HostPlan& plan);
+
+// Device view of one mesh's plan (kernel argument, passed by value).
+struct DevPlan {
+  int dim;
+  int kind;              // pfem_material_kind
+  int n_tiles;
+  int n_halo;
+  int max_local;         // largest tile node count (shared-memory sizing)
+  int slot_cap;          // largest tile incidence count = max tile elements * (dim + 1)
+  int64_t n_nodes;
+  int64_t n_partials;
+  const int4* tile_a;
+  const int4* tile_b;
+  const float4* lnode_f;
+  const PfemDouble4* lnode_d;
+  const uint16_t* slot_off;
+  const ushort4* ecode;
+  const float2* emat_f;
+  const double2* emat_d;
+  const int32_t* halo_info;
+  const int32_t* halo_ptr;
+  const int32_t* halo_src;
+  void* partial;         // scratch: n_partials * dim values of the compute type (x2 for fused)
+  double* tile_energy;   // per-tile strain-energy partials
+  int32_t* inverted;     // count of J <= 0 elements (device int)
+  const double* f_ext;   // n_dofs, FP64, at full load
+  const float* f_ext_f;  // n_dofs, the same rounded to FP32
+  const double* dvalues; // n_dofs prescribed values at full load
+  const uint8_t* dmask;  // n_dofs
+};
+
+// Operation bits of the element-tile kernel.
+enum : int {
+  OP_TANGENT = 1,   // y = A(u) v
+  OP_RESIDUAL = 2,  // r = P (f_int(u) - s f_ext)
+  OP_ENERGY = 4,    // per-tile sum of V Psi
+  OP_DIAG = 8,      // d = diag A(u)
+};
+
+struct OpArgs {
+  const void* u;    // VT*, may be null for linear tangent/diag
+  const void* v;    // VT*
+  void* y;          // VT* tangent output
+  void* r;          // VT* residual output
+  void* d;          // VT* diagonal output
+  double load_scale;
+};
+
+// Launches the tile kernel and the halo pass for one mesh (kernels_tile.cu).
+pfem_status launch_element_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dtype ct,
+                              const OpArgs& a, cudaStream_t s);
+
+// Dynamic shared memory one tile CTA of launch_element_op needs.
+size_t element_op_smem(const DevPlan& P, int ops, pfem_dtype ct);
+
+// Deterministic FP64 reductions (kernels_vec.cu). partials: kReduceBlocks doubles,
+// counter: one zero-initialised unsigned int (reset by the last block).
+// out[0] = sum over tiles of tile_energy; out[1] = out[0] - s * f_ext . u
+pfem_status launch_energy_finalize(const DevPlan& P, pfem_dtype vt, const void* u, double s,
+                                   double* partials, unsigned int* counter, double* out,
+                                   cudaStream_t st);
+
+}  // namespace pfem
+
+struct pfem_mesh_s {
+  pfem::DevPlan plan;
+  pfem_mesh_stats stats;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  double load_scale = 1.0;
+  void* arena = nullptr;     // single device allocation holding every plan array
+  size_t arena_bytes = 0;
+  // small device scratch for reductions
+  double* red_partials = nullptr;   // kReduceBlocks * 4 doubles
+  unsigned int* red_counter = nullptr;
+  double* red_out = nullptr;        // 8 doubles
+  double* host_out = nullptr;       // pinned, 8 doubles
+  int32_t* host_int = nullptr;      // pinned, 4 ints
+  int64_t n_dofs = 0, n_free = 0;
+  void* solver = nullptr;          // solver workspace (solve.cu), created on first solve
+};

@@ -1,0 +1,417 @@
+// Warm-started solvers on the device (Sec. 2.3.2 warm start; App. B linear system and
+// Newton-Raphson with load steps).
+//
+// Jacobi-PCG keeps every vector, dot and norm in FP64 on the GPU; the operator applications
+// inside the iteration run in the requested element precision. With the FP32 operator the
+// recursive residual drifts from the true one at the 1e-7 level, so the iteration stops for
+// an FP64 residual replacement (true residual with the FP64 operator swapped in for the
+// recursive one, search direction kept) whenever the recursive residual has dropped by
+// repl_factor since the last replacement, and before declaring convergence: the stopping
+// rule ||f - K u|| / ref < tol is always confirmed with the FP64 operator.
+//
+// The iteration body (apply, alpha, update, direction) is captured once per mesh into a CUDA
+// graph whose while-conditional node repeats it on the device until the state asks for a
+// replacement or terminates, so the host synchronises only a handful of times per solve.
+// The plain mode (pfem_set_solver_mode(1)) launches the same kernels one iteration at a time
+// with a host-synchronised residual check after each iteration.
+
+#include <cmath>
+#include <cstring>
+
+#include "kernels_vec.cuh"
+#include "pfem_internal.h"
+#include "solver.h"
+
+namespace pfem {
+
+static int g_solver_mode = 0;  // 0 = device while-loop graph, 1 = plain host loop
+
+struct SolverWS {
+  int64_t n = 0;
+  double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *res = nullptr;
+  double *u = nullptr, *rn = nullptr, *tmp = nullptr;
+  PcgState* st = nullptr;    // device
+  PcgState* hst = nullptr;   // pinned host mirror
+  double* dnorm = nullptr;   // device scalar
+  void* block = nullptr;
+  size_t bytes = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [ct][use_u]
+  bool graph_failed = false;
+};
+
+__global__ void set_cond_kernel(cudaGraphConditionalHandle h, const PcgState* st) {
+  cudaGraphSetConditional(h, (st->done == 0 && st->repl == 0) ? 1u : 0u);
+}
+
+__global__ void norm_to_ref_kernel(const double* nrm, PcgState* st) {
+  const double v = *nrm;
+  st->ref = v > 0.0 ? v : 1.0;
+}
+
+static SolverWS* ws_of(pfem_mesh_t m) { return static_cast<SolverWS*>(m->solver); }
+
+size_t solver_bytes(pfem_mesh_t m) { return m && m->solver ? ws_of(m)->bytes : 0; }
+
+void solver_release(pfem_mesh_t m) {
+  SolverWS* w = ws_of(m);
+  if (!w) return;
+  for (auto& row : w->exec)
+    for (auto& e : row)
+      if (e) cudaGraphExecDestroy(e);
+  if (w->cap) cudaStreamDestroy(w->cap);
+  if (w->block) cudaFree(w->block);
+  if (w->hst) cudaFreeHost(w->hst);
+  delete w;
+  m->solver = nullptr;
+}
+
+static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
+  if (m->solver) {
+    *out = ws_of(m);
+    return PFEM_OK;
+  }
+  SolverWS* w = new SolverWS();
+  w->n = m->n_dofs;
+  const size_t vb = ((size_t)w->n * sizeof(double) + 255) & ~size_t(255);
+  w->bytes = 9 * vb + 512;
+  cudaError_t e = cudaMalloc(&w->block, w->bytes);
+  if (e != cudaSuccess) {
+    delete w;
+    return cuda_fail(e, "cudaMalloc(solver workspace)");
+  }
+  char* b = static_cast<char*>(w->block);
+  double** vecs[9] = {&w->x, &w->r, &w->p, &w->q, &w->dinv, &w->res, &w->u, &w->rn, &w->tmp};
+  for (int i = 0; i < 9; ++i) *vecs[i] = reinterpret_cast<double*>(b + i * vb);
+  w->st = reinterpret_cast<PcgState*>(b + 9 * vb);
+  w->dnorm = reinterpret_cast<double*>(b + 9 * vb + 256);
+  e = cudaMallocHost(&w->hst, sizeof(PcgState));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaFree(w->block);
+    if (w->hst) cudaFreeHost(w->hst);
+    delete w;
+    return cuda_fail(e, "solver workspace");
+  }
+  m->solver = w;
+  *out = w;
+  return PFEM_OK;
+}
+
+// One PCG iteration: q = A p, alpha, x/r update (+ flags), new direction.
+static pfem_status pcg_body(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u, cudaStream_t s,
+                            cudaGraphConditionalHandle h, int set_cond) {
+  OpArgs a{use_u ? w->u : nullptr, w->p, w->q, nullptr, nullptr, 1.0};
+  pfem_status st = launch_element_op(m->plan, OP_TANGENT, PFEM_F64, ct, a, s);
+  if (st) return st;
+  if ((st = vk_alpha(w->n, w->p, w->q, w->st, m->red_partials, m->red_counter, s))) return st;
+  if ((st = vk_update(w->n, w->x, w->r, w->p, w->q, w->dinv, w->st, m->red_partials, m->red_counter, h, set_cond, s)))
+    return st;
+  return vk_direction(w->n, w->r, w->dinv, w->p, w->st, s);
+}
+
+static pfem_status build_graph(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  PFEM_CUDA(cudaGraphCreate(&g, 0));
+  auto fail = [&](cudaError_t e) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return cuda_fail(e, "building the PCG while-loop graph");
+  };
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) return fail(e);
+  // pre-node: condition = state still running (so a finished state runs the body zero times)
+  cudaKernelNodeParams kp;
+  std::memset(&kp, 0, sizeof(kp));
+  void* args[2] = {&h, &w->st};
+  kp.func = (void*)set_cond_kernel;
+  kp.gridDim = dim3(1);
+  kp.blockDim = dim3(1);
+  kp.kernelParams = args;
+  cudaGraphNode_t pre, cn;
+  e = cudaGraphAddKernelNode(&pre, g, nullptr, 0, &kp);
+  if (e != cudaSuccess) return fail(e);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  e = cudaGraphAddNode(&cn, g, &pre, nullptr, 1, &cp);
+  if (e != cudaSuccess) return fail(e);
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  e = cudaStreamBeginCaptureToGraph(w->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return fail(e);
+  const pfem_status st = pcg_body(m, w, ct, use_u, w->cap, h, 1);
+  e = cudaStreamEndCapture(w->cap, &body);
+  if (st != PFEM_OK) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return fail(e);
+  e = cudaGraphInstantiate(out, g, 0);
+  if (e != cudaSuccess) return fail(e);
+  cudaGraphDestroy(g);
+  return PFEM_OK;
+}
+
+// Residual for a replacement: linear solve -> res = P (f_int(x) - s f) with the FP64
+// operator; Newton inner solve (A d = -rn) -> res = rn + A64(u) x.
+static pfem_status true_residual(pfem_mesh_t m, SolverWS* w, bool newton_inner, cudaStream_t s) {
+  if (!newton_inner) {
+    OpArgs a{w->x, nullptr, nullptr, w->res, nullptr, m->load_scale};
+    return launch_element_op(m->plan, OP_RESIDUAL, PFEM_F64, PFEM_F64, a, s);
+  }
+  OpArgs a{w->u, w->x, w->res, nullptr, nullptr, 1.0};
+  pfem_status st = launch_element_op(m->plan, OP_TANGENT, PFEM_F64, PFEM_F64, a, s);
+  if (st) return st;
+  return vk_axpy(w->n, 1.0, w->rn, w->res, s);
+}
+
+static pfem_status read_state(pfem_mesh_t m, SolverWS* w) {
+  PFEM_CUDA(cudaMemcpyAsync(w->hst, w->st, sizeof(PcgState), cudaMemcpyDeviceToHost, m->stream));
+  PFEM_CUDA(cudaStreamSynchronize(m->stream));
+  return PFEM_OK;
+}
+
+// Runs PCG from the current x (dinv, ref, tol, max_iter already set in the device state).
+static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u, bool newton_inner) {
+  cudaStream_t s = m->stream;
+  pfem_status st;
+  PFEM_CUDA(cudaMemsetAsync(w->p, 0, (size_t)w->n * sizeof(double), s));
+  if ((st = true_residual(m, w, newton_inner, s))) return st;
+  if ((st = vk_replace(w->n, w->res, w->r, w->dinv, w->st, 1, m->red_partials, m->red_counter, s))) return st;
+  if ((st = vk_direction(w->n, w->r, w->dinv, w->p, w->st, s))) return st;
+  cudaGraphExec_t* ex = &w->exec[ct == PFEM_F64][use_u ? 1 : 0];
+  const bool use_graph = g_solver_mode == 0 && !w->graph_failed;
+  if (use_graph && !*ex) {
+    if (build_graph(m, w, ct, use_u, ex) != PFEM_OK) {
+      w->graph_failed = true;
+      *ex = nullptr;
+    }
+  }
+  for (;;) {
+    if ((st = read_state(m, w))) return st;
+    if (w->hst->done != 0) break;
+    if (w->hst->repl != 0) {
+      if ((st = true_residual(m, w, newton_inner, s))) return st;
+      if ((st = vk_replace(w->n, w->res, w->r, w->dinv, w->st, 0, m->red_partials, m->red_counter, s))) return st;
+      if ((st = vk_direction(w->n, w->r, w->dinv, w->p, w->st, s))) return st;
+      continue;
+    }
+    if (use_graph && *ex) {
+      PFEM_CUDA(cudaGraphLaunch(*ex, s));
+    } else {
+      if ((st = pcg_body(m, w, ct, use_u, s, cudaGraphConditionalHandle(), 0))) return st;
+    }
+  }
+  return PFEM_OK;
+}
+
+static pfem_status set_state(pfem_mesh_t m, SolverWS* w, double tol, int max_iter) {
+  PcgState h;
+  std::memset(&h, 0, sizeof(h));
+  h.tol = tol;
+  h.max_iter = max_iter;
+  h.repl_factor = 1e-2;
+  h.repl_threshold = 0.0;
+  h.ref = 1.0;
+  *w->hst = h;
+  PFEM_CUDA(cudaMemcpyAsync(w->st, w->hst, sizeof(PcgState), cudaMemcpyHostToDevice, m->stream));
+  PFEM_CUDA(cudaStreamSynchronize(m->stream));  // the pinned mirror is reused right away
+  return PFEM_OK;
+}
+
+// ref = ||P (f_int(u_lift) - s f)||, u_lift = prescribed values (x s) with zero free DOFs.
+static pfem_status reference_norm(pfem_mesh_t m, SolverWS* w, double scale) {
+  cudaStream_t s = m->stream;
+  pfem_status st;
+  if ((st = vk_lift(w->n, nullptr, m->plan.dvalues, m->plan.dmask, scale, w->tmp, s))) return st;
+  OpArgs a{w->tmp, nullptr, nullptr, w->res, nullptr, scale};
+  if ((st = launch_element_op(m->plan, OP_RESIDUAL, PFEM_F64, PFEM_F64, a, s))) return st;
+  if ((st = vk_norm2(w->n, w->res, w->dnorm, m->red_partials, m->red_counter, s))) return st;
+  norm_to_ref_kernel<<<1, 1, 0, s>>>(w->dnorm, w->st);
+  PFEM_CUDA(cudaGetLastError());
+  return PFEM_OK;
+}
+
+static pfem_status jacobi(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, const double* u) {
+  // the diagonal lands in q (FP64), then dinv = 1 / d
+  OpArgs a{u, nullptr, nullptr, nullptr, w->q, 1.0};
+  pfem_status st = launch_element_op(m->plan, OP_DIAG, PFEM_F64, ct, a, m->stream);
+  if (st) return st;
+  return vk_invert_diag(w->n, w->q, PFEM_F64, w->dinv, m->stream);
+}
+
+static pfem_status status_of(int done) {
+  switch (done) {
+    case PCG_CONVERGED: return PFEM_OK;
+    case PCG_MAXITER: return PFEM_ERR_NOT_CONVERGED;
+    case PCG_NONFINITE: return PFEM_ERR_NONFINITE;
+    default: return PFEM_ERR_NOT_CONVERGED;
+  }
+}
+
+}  // namespace pfem
+
+using namespace pfem;
+
+extern "C" {
+
+pfem_status pfem_set_solver_mode(int32_t mode) {
+  if (mode != 0 && mode != 1) {
+    set_error("solver mode must be 0 (graph) or 1 (plain)");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  g_solver_mode = mode;
+  return PFEM_OK;
+}
+
+pfem_status pfem_solve_linear(pfem_mesh_t m, pfem_dtype dt, const double* u0, double tol, int32_t max_iter,
+                              double* u_out, pfem_solve_info* info) {
+  pfem_status st = check_mesh(m);
+  if (st) return st;
+  if (m->plan.kind != PFEM_LINEAR) {
+    set_error("pfem_solve_linear needs a linear-elastic mesh (use pfem_solve_newton)");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  if (!u_out || !(tol > 0.0) || max_iter < 0 || (dt != PFEM_F32 && dt != PFEM_F64)) {
+    set_error("invalid solve arguments");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  SolverWS* w;
+  if ((st = ws_get(m, &w))) return st;
+  cudaStream_t s = m->stream;
+  if ((st = set_state(m, w, tol, max_iter))) return st;
+  if ((st = reference_norm(m, w, m->load_scale))) return st;
+  if ((st = jacobi(m, w, dt, nullptr))) return st;
+  if ((st = vk_lift(w->n, u0, m->plan.dvalues, m->plan.dmask, m->load_scale, w->x, s))) return st;
+  if ((st = pcg_run(m, w, dt, false, false))) return st;
+  PFEM_CUDA(cudaMemcpyAsync(u_out, w->x, (size_t)w->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if ((st = read_state(m, w))) return st;
+  const PcgState& h = *w->hst;
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iterations = h.iter;
+    info->replacements = h.replacements;
+    info->rel_residual_recursive = h.rel;
+    info->rel_residual_true_f64 = h.rel_true;
+    info->reference_norm = h.ref;
+  }
+  st = status_of(h.done);
+  if (info) info->status = st;
+  if (st) set_error("PCG stopped with state %d after %d iterations (rel %g)", h.done, h.iter, h.rel_true);
+  return st;
+}
+
+pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, double tol, int32_t n_load_steps,
+                              int32_t max_newton, double inner_tol, double* u_out, pfem_solve_info* info) {
+  pfem_status st = check_mesh(m);
+  if (st) return st;
+  if (!u_out || !(tol > 0.0) || !(inner_tol > 0.0) || n_load_steps < 1 || max_newton < 1 ||
+      (dt != PFEM_F32 && dt != PFEM_F64)) {
+    set_error("invalid Newton arguments");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  SolverWS* w;
+  if ((st = ws_get(m, &w))) return st;
+  cudaStream_t s = m->stream;
+  const double saved_scale = m->load_scale;
+  const int64_t n = w->n;
+  int total_inner = 0, n_newton = 0, n_repl = 0, n_back = 0;
+  double init_rel = -1.0, final_rel = 0.0, ref = 1.0;
+  pfem_status result = PFEM_OK;
+  if (u0) PFEM_CUDA(cudaMemcpyAsync(w->u, u0, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  else PFEM_CUDA(cudaMemsetAsync(w->u, 0, (size_t)n * sizeof(double), s));
+  const int inner_max = (int)std::min<int64_t>(10 * n + 100, 1000000);
+  for (int step = 1; step <= n_load_steps && result == PFEM_OK; ++step) {
+    const double scale = saved_scale * (double)step / (double)n_load_steps;
+    m->load_scale = scale;
+    if ((st = vk_lift(n, w->u, m->plan.dvalues, m->plan.dmask, scale, w->u, s))) break;
+    if ((st = set_state(m, w, inner_tol, inner_max))) break;
+    if ((st = reference_norm(m, w, scale))) break;
+    if ((st = read_state(m, w))) break;
+    ref = w->hst->ref;
+    for (int it = 0;; ++it) {
+      OpArgs a{w->u, nullptr, nullptr, w->rn, nullptr, scale};
+      if ((st = launch_element_op(m->plan, OP_RESIDUAL, PFEM_F64, PFEM_F64, a, s))) break;
+      if ((st = vk_norm2(n, w->rn, w->dnorm, m->red_partials, m->red_counter, s))) break;
+      PFEM_CUDA(cudaMemcpyAsync(m->host_out, w->dnorm, sizeof(double), cudaMemcpyDeviceToHost, s));
+      PFEM_CUDA(cudaStreamSynchronize(s));
+      const double rel = m->host_out[0] / ref;
+      if (init_rel < 0) init_rel = rel;
+      final_rel = rel;
+      if (!std::isfinite(rel)) {
+        result = PFEM_ERR_NONFINITE;
+        break;
+      }
+      if (rel <= tol) break;
+      if (it >= max_newton) {
+        result = PFEM_ERR_NOT_CONVERGED;
+        set_error("Newton: %d iterations in load step %d, rel residual %g", it, step, rel);
+        break;
+      }
+      // inner solve A(u) d = -rn from d = 0 to inner_tol relative to ||rn||
+      if ((st = set_state(m, w, inner_tol, inner_max))) break;
+      PFEM_CUDA(cudaMemcpyAsync(&w->st->ref, w->dnorm, sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if ((st = jacobi(m, w, dt, w->u))) break;
+      PFEM_CUDA(cudaMemsetAsync(w->x, 0, (size_t)n * sizeof(double), s));
+      if ((st = pcg_run(m, w, dt, true, true))) break;
+      if ((st = read_state(m, w))) break;
+      total_inner += w->hst->iter;
+      n_repl += w->hst->replacements;
+      if (w->hst->done != PCG_CONVERGED && w->hst->done != PCG_MAXITER) {
+        result = status_of(w->hst->done);
+        set_error("inner PCG failed with state %d", w->hst->done);
+        break;
+      }
+      // step with halving while any element would invert
+      double t = 1.0;
+      bool ok = false;
+      for (int k = 0; k <= 10; ++k) {
+        PFEM_CUDA(cudaMemcpyAsync(w->tmp, w->u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        if ((st = vk_axpy(n, t, w->x, w->tmp, s))) break;
+        PFEM_CUDA(cudaMemsetAsync(m->plan.inverted, 0, sizeof(int32_t), s));
+        OpArgs ea{w->tmp, nullptr, nullptr, nullptr, nullptr, scale};
+        if ((st = launch_element_op(m->plan, OP_ENERGY, PFEM_F64, PFEM_F64, ea, s))) break;
+        PFEM_CUDA(cudaMemcpyAsync(m->host_int, m->plan.inverted, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        PFEM_CUDA(cudaStreamSynchronize(s));
+        if (m->host_int[0] == 0) {
+          ok = true;
+          break;
+        }
+        ++n_back;
+        t *= 0.5;
+      }
+      if (st) break;
+      if (!ok) {
+        result = PFEM_ERR_INVERTED;
+        set_error("Newton: every trial step inverts an element");
+        break;
+      }
+      PFEM_CUDA(cudaMemcpyAsync(w->u, w->tmp, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      ++n_newton;
+    }
+    if (st) break;
+  }
+  m->load_scale = saved_scale;
+  if (st) return st;
+  PFEM_CUDA(cudaMemcpyAsync(u_out, w->u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  PFEM_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iterations = total_inner;
+    info->newton_iterations = n_newton;
+    info->replacements = n_repl;
+    info->inverted_backtracks = n_back;
+    info->rel_residual_recursive = final_rel;
+    info->rel_residual_true_f64 = final_rel;
+    info->initial_rel_residual = init_rel;
+    info->reference_norm = ref;
+    info->status = result;
+  }
+  return result;
+}
+
+}  // extern "C"

@@ -92,15 +92,20 @@ def boundary_facets(coords, conn, axis=None, value=None, tol=1e-9):
     |coords[:, axis] - value| <= tol. Returns (F, dim) int32.
     """
     nv = conn.shape[1]
+    if axis is not None:
+        # keep only elements with at least nv-1 nodes on the plane, then their on-plane faces
+        # (all copies of a face share its nodes, so counting among them is exact)
+        on_node = np.abs(coords[:, axis] - value) <= tol
+        conn = conn[on_node[conn].sum(axis=1) >= nv - 1]
     faces = np.concatenate([np.delete(conn, a, axis=1) for a in range(nv)], axis=0)
+    if axis is not None:
+        faces = faces[np.all(on_node[faces], axis=1)]
+    if faces.shape[0] == 0:
+        return np.zeros((0, nv - 1), dtype=np.int32)
     key = np.sort(faces, axis=1)
     _, inv, counts = np.unique(key, axis=0, return_inverse=True, return_counts=True)
     inv = inv.ravel()
-    bnd = faces[counts[inv] == 1]
-    if axis is not None:
-        on = np.all(np.abs(coords[bnd][:, :, axis] - value) <= tol, axis=1)
-        bnd = bnd[on]
-    return bnd.astype(np.int32)
+    return faces[counts[inv] == 1].astype(np.int32)
 
 
 def jitter_nodes(coords, conn, amount, h, rng, fixed=None):

@@ -1,0 +1,159 @@
+"""GPU parity of the warm-started solvers against the FP64 CPU oracle (through the C ABI).
+
+Bars: solution relative L2 <= 1e-6 at residual tolerance 1e-8 (1e-10 for the FP64 plate),
+PCG iteration counts within +-2 of the oracle's Jacobi-PCG, and the FP64 true residual of
+the returned solution below tol.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import pfem_inputs as pi
+from oracle import fem, solve
+from tests.gpu_util import dev, host, pfem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _linear_case(p, tol, precision, u0=None, K=None, max_iter=100000):
+    m = fem.Mesh(p)
+    K = fem.assemble_linear_K(m) if K is None else K
+    u_ref, it_ref, _ = solve.solve_linear(m, u0=u0, tol=tol, K=K)
+    P = pfem()
+    mesh = P.Mesh(p)
+    u, info = P.pfem_solve_linear(mesh, None if u0 is None else dev(u0), tol=tol, max_iter=max_iter,
+                                  precision=precision)
+    return m, host(u), info, u_ref, it_ref
+
+
+def test_plate_fp64_zero_start():
+    p = pi.cfg1_plate()
+    m, u, info, u_ref, it_ref = _linear_case(p, 1e-10, "f64")
+    assert abs(info["iterations"] - it_ref) <= 2, (info, it_ref)
+    assert rel_l2(u, u_ref) <= 1e-8
+    assert info["rel_residual_true_f64"] < 1e-10
+    u_direct = solve.solve_linear_direct(m)
+    assert rel_l2(u, u_direct) <= 1e-6
+
+
+@pytest.mark.parametrize("warm", [False, True], ids=["zero", "warm"])
+def test_small_cube_fp32(warm):
+    p = pi.cube_problem(12, seed=2)
+    m = fem.Mesh(p)
+    K = fem.assemble_linear_K(m)
+    u0 = None
+    if warm:
+        u_star, _, _ = solve.solve_linear(m, tol=1e-13, K=K)
+        u0 = pi.make_warm_start(p, u_star, seed=20)
+    m, u, info, u_ref, it_ref = _linear_case(p, 1e-8, "f32", u0=u0, K=K)
+    assert abs(info["iterations"] - it_ref) <= 2, (info, it_ref)
+    assert rel_l2(u, u_ref) <= 1e-6
+    assert info["rel_residual_true_f64"] < 1e-8
+
+
+def test_solver_modes_bitwise_equal_and_deterministic():
+    P = pfem()
+    p = pi.cube_problem(8, seed=3)
+    mesh = P.Mesh(p)
+    outs = []
+    for mode in (0, 0, 1):
+        P.pfem_set_solver_mode(mode)
+        u, info = P.pfem_solve_linear(mesh, tol=1e-8)
+        outs.append((host(u), info["iterations"]))
+    P.pfem_set_solver_mode(0)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][0], outs[2][0])
+    assert outs[0][1] == outs[1][1] == outs[2][1]
+
+
+def test_skip_test_returns_without_iterating():
+    P = pfem()
+    p = pi.cube_problem(6, seed=4)
+    m = fem.Mesh(p)
+    u_star, _, _ = solve.solve_linear(m, tol=1e-14)
+    mesh = P.Mesh(p)
+    u, info = P.pfem_solve_linear(mesh, dev(u_star), tol=1e-8, precision="f64")
+    assert info["iterations"] == 0
+    assert rel_l2(host(u), u_star) <= 1e-14
+
+
+def test_not_converged_status():
+    P = pfem()
+    p = pi.cube_problem(6, seed=5)
+    mesh = P.Mesh(p)
+    u, info = P.pfem_solve_linear(mesh, tol=1e-12, max_iter=5, raise_on_error=False)
+    assert info["status"] == 5 and info["iterations"] == 5
+
+
+@pytest.fixture(scope="module")
+def cfg2_oracle():
+    p = pi.cfg2_cube()
+    m = fem.Mesh(p)
+    K = fem.assemble_linear_K(m)
+    u_star, _, _ = solve.solve_linear(m, tol=1e-12, K=K)
+    warm = pi.make_warm_start(p, u_star, seed=20)
+    return p, m, K, u_star, warm
+
+
+@pytest.mark.parametrize("warm", [False, True], ids=["zero", "warm"])
+def test_cfg2_full_size(cfg2_oracle, warm):
+    p, m, K, u_star, warm_u = cfg2_oracle
+    u0 = warm_u if warm else None
+    _, u, info, u_ref, it_ref = _linear_case(p, 1e-8, "f32", u0=u0, K=K)
+    assert abs(info["iterations"] - it_ref) <= 2, (info, it_ref)
+    assert rel_l2(u, u_ref) <= 1e-6
+    assert info["rel_residual_true_f64"] < 1e-8
+
+
+# --------------------------------------------------------------------------- Newton
+
+
+@pytest.fixture(scope="module")
+def bar_oracle():
+    p = pi.bar_problem(24, 6, 6, seed=3)
+    m = fem.Mesh(p)
+    u5, n5, _ = solve.solve_newton(m, tol=1e-8, n_load_steps=5)
+    u_star, _, _ = solve.solve_newton(m, u0=u5, tol=1e-12, n_load_steps=1, inner_tol=1e-12)
+    warm = pi.make_warm_start(p, u_star, seed=30)
+    uw, nw, _ = solve.solve_newton(m, u0=warm, tol=1e-8, n_load_steps=1)
+    return p, m, u5, n5, u_star, warm, uw, nw
+
+
+def test_newton_zero_start_load_steps(bar_oracle):
+    p, m, u5, n5, u_star, warm, uw, nw = bar_oracle
+    P = pfem()
+    mesh = P.Mesh(p)
+    u, info = P.pfem_solve_newton(mesh, tol=1e-8, n_load_steps=5, inner_tol=1e-8)
+    assert abs(info["newton_iterations"] - n5) <= 2, (info, n5)
+    assert rel_l2(host(u), u_star) <= 1e-6
+    assert info["rel_residual_true_f64"] <= 1e-8
+
+
+def test_newton_warm_start(bar_oracle):
+    p, m, u5, n5, u_star, warm, uw, nw = bar_oracle
+    P = pfem()
+    mesh = P.Mesh(p)
+    u, info = P.pfem_solve_newton(mesh, dev(warm), tol=1e-8, n_load_steps=1, inner_tol=1e-8)
+    assert abs(info["newton_iterations"] - nw) <= 1, (info, nw)
+    assert info["newton_iterations"] < n5
+    assert rel_l2(host(u), u_star) <= 1e-6
+    r = fem.residual(m, host(u))
+    assert np.linalg.norm(r) <= 1e-8 * solve.newton_reference(m, 1.0) * 1.0001
+
+
+def test_cfg3_full_size_warm_newton_residual():
+    """Full 98,304-tet bar: the warm-started Newton solution satisfies the oracle's residual
+    test (a property that holds at any size) and keeps every element uninverted."""
+    P = pfem()
+    p = pi.cfg3_bar()
+    m = fem.Mesh(p)
+    mesh = P.Mesh(p)
+    u5, info5 = P.pfem_solve_newton(mesh, tol=1e-8, n_load_steps=5)
+    warm = pi.make_warm_start(p, host(u5), seed=30)
+    u, info = P.pfem_solve_newton(mesh, dev(warm), tol=1e-8, n_load_steps=1)
+    uh = host(u)
+    ref = solve.newton_reference(m, 1.0)
+    assert np.linalg.norm(fem.residual(m, uh)) <= 1.01e-8 * ref
+    assert fem.min_jacobian(m, uh) > 0
+    assert info["newton_iterations"] < info5["newton_iterations"]
+    assert rel_l2(uh, host(u5)) <= 1e-6
