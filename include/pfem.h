@@ -98,6 +98,7 @@ typedef struct {
   double initial_rel_residual;     /* ||r(u0)|| / ref, the Sec. 2.3.2 skip-test quantity */
   double reference_norm;           /* ref = ||r(u_lift)||: zero free DOFs, prescribed values */
   pfem_status status;
+  int64_t kernel_launches;         /* kernels this solve ran (graph replays included) */
 } pfem_solve_info;
 
 /* ---- mesh ------------------------------------------------------------------------ */

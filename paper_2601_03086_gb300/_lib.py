@@ -71,6 +71,7 @@ class SolveInfo(C.Structure):
         ("initial_rel_residual", C.c_double),
         ("reference_norm", C.c_double),
         ("status", C.c_int32),
+        ("kernel_launches", C.c_int64),
     ]
 
 

@@ -363,13 +363,13 @@ static pfem_status run(const DevPlan& P, const OpArgs& A, cudaStream_t s) {
       set_error("tile needs %zu bytes of shared memory", L.total);
       return PFEM_ERR_UNSUPPORTED;
     }
-    tile_kernel<DIM, KIND, OPS, VT, CT><<<P.n_tiles, kThreads, L.total, s>>>(P, A);
+    tile_kernel<DIM, KIND, OPS, VT, CT><<<P.n_tiles, kThreads, L.total, s>>>(P, A); PFEM_COUNT_LAUNCH();
     PFEM_CUDA(cudaGetLastError());
   }
   constexpr int HOPS = OPS & (OP_RESIDUAL | OP_TANGENT | OP_DIAG);
   if constexpr (HOPS != 0) {
     if (P.n_halo > 0) {
-      halo_kernel<DIM, HOPS, VT, CT><<<(P.n_halo + 255) / 256, 256, 0, s>>>(P, A);
+      halo_kernel<DIM, HOPS, VT, CT><<<(P.n_halo + 255) / 256, 256, 0, s>>>(P, A); PFEM_COUNT_LAUNCH();
       PFEM_CUDA(cudaGetLastError());
     }
   }

@@ -32,6 +32,7 @@ pfem_status launch_energy_finalize(const DevPlan& P, pfem_dtype vt, const void* 
   else
     energy_finalize_kernel<double><<<kReduceBlocks, kReduceThreads, 0, st>>>(
         P.n_tiles, P.tile_energy, nd, P.f_ext, static_cast<const double*>(u), s, partials, counter, out);
+  PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
@@ -63,8 +64,10 @@ __global__ void __launch_bounds__(kReduceThreads)
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     v[0] += p[i] * q[i];
   if (grid_sum<1>(v, partials, counter, scratch) && threadIdx.x == 0) {
+    // Negative curvature (an indefinite tangent far from equilibrium) does not stop the
+    // iteration, as in plain CG; only p.q = 0 or a non-finite value does.
     const double pq = v[0];
-    if (!(pq > 0.0) || !isfinite(pq)) {
+    if (pq == 0.0 || !isfinite(pq)) {
       st->alpha = 0.0;
       st->done = isfinite(pq) ? PCG_BREAKDOWN : PCG_NONFINITE;
     } else {
@@ -178,7 +181,7 @@ static inline int vec_grid(int64_t n) {
 
 pfem_status vk_lift(int64_t n, const double* u0, const double* values, const uint8_t* mask, double s, double* x,
                     cudaStream_t st) {
-  lift_kernel<<<vec_grid(n), 256, 0, st>>>(n, u0, values, mask, s, x);
+  lift_kernel<<<vec_grid(n), 256, 0, st>>>(n, u0, values, mask, s, x); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
@@ -186,13 +189,14 @@ pfem_status vk_lift(int64_t n, const double* u0, const double* values, const uin
 pfem_status vk_invert_diag(int64_t n, const void* d, pfem_dtype dt, double* dinv, cudaStream_t st) {
   if (dt == PFEM_F32) invert_diag_kernel<float><<<vec_grid(n), 256, 0, st>>>(n, static_cast<const float*>(d), dinv);
   else invert_diag_kernel<double><<<vec_grid(n), 256, 0, st>>>(n, static_cast<const double*>(d), dinv);
+  PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
 
 pfem_status vk_alpha(int64_t n, const double* p, const double* q, PcgState* st, double* partials,
                      unsigned int* counter, cudaStream_t s) {
-  pcg_alpha_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, p, q, st, partials, counter);
+  pcg_alpha_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, p, q, st, partials, counter); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
@@ -201,40 +205,40 @@ pfem_status vk_update(int64_t n, double* x, double* r, const double* p, const do
                       PcgState* st, double* partials, unsigned int* counter, cudaGraphConditionalHandle cond,
                       int set_cond, cudaStream_t s) {
   pcg_update_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, x, r, p, q, dinv, st, partials, counter, cond,
-                                                            set_cond);
+                                                            set_cond); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
 
 pfem_status vk_direction(int64_t n, const double* r, const double* dinv, double* p, const PcgState* st,
                          cudaStream_t s) {
-  pcg_direction_kernel<<<vec_grid(n), 256, 0, s>>>(n, r, dinv, p, st);
+  pcg_direction_kernel<<<vec_grid(n), 256, 0, s>>>(n, r, dinv, p, st); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
 
 pfem_status vk_replace(int64_t n, const double* res, double* r, const double* dinv, PcgState* st, int restart,
                        double* partials, unsigned int* counter, cudaStream_t s) {
-  pcg_replace_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, res, r, dinv, st, restart, partials, counter);
+  pcg_replace_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, res, r, dinv, st, restart, partials, counter); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
 
 pfem_status vk_norm2(int64_t n, const double* v, double* out, double* partials, unsigned int* counter,
                      cudaStream_t s) {
-  norm2_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, v, out, partials, counter);
+  norm2_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, v, out, partials, counter); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
 
 pfem_status vk_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
-  axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, a, x, y);
+  axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, a, x, y); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
 
 pfem_status vk_scale_copy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
-  scale_copy_kernel<<<vec_grid(n), 256, 0, s>>>(n, a, x, y);
+  scale_copy_kernel<<<vec_grid(n), 256, 0, s>>>(n, a, x, y); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }

@@ -48,6 +48,11 @@ constexpr uint32_t kInfoIdMask = (1u << kInfoIdBits) - 1u;
 constexpr int kThreads = 256;      // threads per tile CTA
 constexpr int kReduceBlocks = 296; // fixed grid of the deterministic FP64 reductions (2 x 148)
 
+// Kernels enqueued by this thread (launches recorded into a graph are counted by the caller
+// per replay instead, see solve.cu).
+extern thread_local int64_t g_kernel_launches;
+#define PFEM_COUNT_LAUNCH() (++::pfem::g_kernel_launches)
+
 void set_error(const char* fmt, ...);
 pfem_status cuda_fail(cudaError_t e, const char* what);
 

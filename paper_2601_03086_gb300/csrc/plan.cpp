@@ -21,6 +21,7 @@
 namespace pfem {
 
 static thread_local std::string g_last_error;
+thread_local int64_t g_kernel_launches = 0;
 
 void set_error(const char* fmt, ...) {
   char buf[1024];

@@ -37,6 +37,7 @@ struct SolverWS {
   size_t bytes = 0;
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [ct][use_u]
+  int64_t body_kernels[2][2] = {{0, 0}, {0, 0}};  // kernels per captured iteration
   bool graph_failed = false;
 };
 
@@ -142,7 +143,10 @@ static pfem_status build_graph(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool u
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   e = cudaStreamBeginCaptureToGraph(w->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return fail(e);
+  const int64_t before = g_kernel_launches;
   const pfem_status st = pcg_body(m, w, ct, use_u, w->cap, h, 1);
+  w->body_kernels[ct == PFEM_F64][use_u ? 1 : 0] = g_kernel_launches - before;
+  g_kernel_launches = before;  // captured, not run: replays are counted per launch
   e = cudaStreamEndCapture(w->cap, &body);
   if (st != PFEM_OK) {
     cudaGetLastError();
@@ -191,8 +195,14 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
       *ex = nullptr;
     }
   }
+  int pending_iter0 = -1;  // iteration count before the last graph launch
+  const int64_t body = w->body_kernels[ct == PFEM_F64][use_u ? 1 : 0];
   for (;;) {
     if ((st = read_state(m, w))) return st;
+    if (pending_iter0 >= 0) {  // a graph replay ran (iterations x body) + the pre-node
+      g_kernel_launches += (int64_t)(w->hst->iter - pending_iter0) * body + 1;
+      pending_iter0 = -1;
+    }
     if (w->hst->done != 0) break;
     if (w->hst->repl != 0) {
       if ((st = true_residual(m, w, newton_inner, s))) return st;
@@ -201,6 +211,7 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
       continue;
     }
     if (use_graph && *ex) {
+      pending_iter0 = w->hst->iter;
       PFEM_CUDA(cudaGraphLaunch(*ex, s));
     } else {
       if ((st = pcg_body(m, w, ct, use_u, s, cudaGraphConditionalHandle(), 0))) return st;
@@ -231,7 +242,7 @@ static pfem_status reference_norm(pfem_mesh_t m, SolverWS* w, double scale) {
   OpArgs a{w->tmp, nullptr, nullptr, w->res, nullptr, scale};
   if ((st = launch_element_op(m->plan, OP_RESIDUAL, PFEM_F64, PFEM_F64, a, s))) return st;
   if ((st = vk_norm2(w->n, w->res, w->dnorm, m->red_partials, m->red_counter, s))) return st;
-  norm_to_ref_kernel<<<1, 1, 0, s>>>(w->dnorm, w->st);
+  norm_to_ref_kernel<<<1, 1, 0, s>>>(w->dnorm, w->st); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
@@ -281,6 +292,7 @@ pfem_status pfem_solve_linear(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
     return PFEM_ERR_INVALID_ARG;
   }
   SolverWS* w;
+  const int64_t launches0 = g_kernel_launches;
   if ((st = ws_get(m, &w))) return st;
   cudaStream_t s = m->stream;
   if ((st = set_state(m, w, tol, max_iter))) return st;
@@ -300,7 +312,10 @@ pfem_status pfem_solve_linear(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
     info->reference_norm = h.ref;
   }
   st = status_of(h.done);
-  if (info) info->status = st;
+  if (info) {
+    info->status = st;
+    info->kernel_launches = g_kernel_launches - launches0;
+  }
   if (st) set_error("PCG stopped with state %d after %d iterations (rel %g)", h.done, h.iter, h.rel_true);
   return st;
 }
@@ -315,6 +330,7 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
     return PFEM_ERR_INVALID_ARG;
   }
   SolverWS* w;
+  const int64_t launches0 = g_kernel_launches;
   if ((st = ws_get(m, &w))) return st;
   cudaStream_t s = m->stream;
   const double saved_scale = m->load_scale;
@@ -410,6 +426,7 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
     info->initial_rel_residual = init_rel;
     info->reference_norm = ref;
     info->status = result;
+    info->kernel_launches = g_kernel_launches - launches0;
   }
   return result;
 }
