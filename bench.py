@@ -193,6 +193,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the 160^3 cube, Newton and CPU-oracle extras")
+    ap.add_argument("--solver-mode", default="graph", choices=["graph", "plain"],
+                    help="plain: one launch per kernel (for per-kernel profiler launch lists)")
     ap.add_argument("--oracle-worker", nargs=2, type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_worker is not None:
@@ -245,6 +247,8 @@ def main():
     def flush_l2():
         flush.fill_(1.0)
 
+    if args.solver_mode == "plain":
+        P.pfem_set_solver_mode(1)
     for i in range(args.warmup):
         P.pfem_solve_linear(mesh, warm_d[i], tol=TOL, u_out=u_out)
     torch.cuda.synchronize()
@@ -308,7 +312,7 @@ def main():
             b.record()
             b.synchronize()
             plain_ms.append(a.elapsed_time(b))
-        P.pfem_set_solver_mode(0)
+        P.pfem_set_solver_mode(1 if args.solver_mode == "plain" else 0)
         zero_ms, zero_it = [], []
         for i in range(2):
             flush_l2()
@@ -338,12 +342,12 @@ def main():
         v64 = torch.randn(n, dtype=torch.float64, device="cuda")
         y64 = torch.empty_like(v64)
         for _ in range(5):
-            P.pfem_tangent_apply(mesh, None, v64, y64)
+            P.pfem_tangent_apply(mesh, None, v64, y64, arith="f32")
         a, b = _events(torch)
         reps = 200
         a.record()
         for _ in range(reps):
-            P.pfem_tangent_apply(mesh, None, v64, y64)
+            P.pfem_tangent_apply(mesh, None, v64, y64, arith="f32")
         b.record()
         b.synchronize()
         us = a.elapsed_time(b) * 1e3 / reps
@@ -363,7 +367,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": WORKLOAD,
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8},
         "gpu_launches": int(sum(i["kernel_launches"] for i in infos)),
-        "clocks": clocks, "all_converged": ok,
+        "clocks": clocks, "all_converged": ok, "solver_mode": args.solver_mode,
     }
     if rank == 0:
         line["roofline"] = extras.pop("roofline")

@@ -54,7 +54,10 @@ typedef enum {
 } pfem_status;
 
 typedef enum { PFEM_LINEAR = 0, PFEM_NEOHOOKEAN = 1 } pfem_material_kind;
-typedef enum { PFEM_F32 = 0, PFEM_F64 = 1 } pfem_dtype;
+/* Vector element type and element arithmetic: F32 = float vectors, FP32 arithmetic;
+ * F64 = double vectors, FP64 arithmetic; F64_F32 = double vectors, FP32 element arithmetic
+ * (the operator the FP32 solvers apply to their FP64 iterates). Sums of energies are FP64. */
+typedef enum { PFEM_F32 = 0, PFEM_F64 = 1, PFEM_F64_F32 = 2 } pfem_dtype;
 
 typedef struct pfem_mesh_s* pfem_mesh_t;
 

@@ -22,7 +22,7 @@ STATUS = {
     11: "PFEM_ERR_UNSUPPORTED",
 }
 PFEM_LINEAR, PFEM_NEOHOOKEAN = 0, 1
-PFEM_F32, PFEM_F64 = 0, 1
+PFEM_F32, PFEM_F64, PFEM_F64_F32 = 0, 1, 2
 
 
 class MeshDesc(C.Structure):

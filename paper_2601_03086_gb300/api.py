@@ -21,11 +21,12 @@ def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
 
-def _dtype_of(t):
+def _dtype_of(t, arith=None):
+    """float32 -> PFEM_F32; float64 -> PFEM_F64, or PFEM_F64_F32 when arith == "f32"."""
     if t.dtype == torch.float32:
         return PFEM_F32
     if t.dtype == torch.float64:
-        return PFEM_F64
+        return _lib.PFEM_F64_F32 if arith == "f32" else PFEM_F64
     raise TypeError("vectors must be float32 or float64 CUDA tensors (got %s)" % t.dtype)
 
 
@@ -128,32 +129,32 @@ def pfem_mesh_set_load_scale(mesh, s):
     check(lib().pfem_mesh_set_load_scale(mesh.handle, float(s)))
 
 
-def pfem_energy(mesh, u):
+def pfem_energy(mesh, u, arith=None):
     """(Pi(u), strain energy) as Python floats (synchronises the mesh stream)."""
     e = C.c_double()
     es = C.c_double()
-    check(lib().pfem_energy(mesh.handle, _dtype_of(u), _dev(u, mesh.n_dofs, "u"), C.byref(e), C.byref(es)))
+    check(lib().pfem_energy(mesh.handle, _dtype_of(u, arith), _dev(u, mesh.n_dofs, "u"), C.byref(e), C.byref(es)))
     return e.value, es.value
 
 
-def pfem_residual(mesh, u, r=None):
+def pfem_residual(mesh, u, r=None, arith=None):
     r = torch.empty_like(u) if r is None else r
-    check(lib().pfem_residual(mesh.handle, _dtype_of(u), _dev(u, mesh.n_dofs, "u"), _dev(r, mesh.n_dofs, "r")))
+    check(lib().pfem_residual(mesh.handle, _dtype_of(u, arith), _dev(u, mesh.n_dofs, "u"), _dev(r, mesh.n_dofs, "r")))
     return r
 
 
-def pfem_tangent_apply(mesh, u, v, y=None):
+def pfem_tangent_apply(mesh, u, v, y=None, arith=None):
     y = torch.empty_like(v) if y is None else y
     up = _dev(u, mesh.n_dofs, "u") if u is not None else None
-    check(lib().pfem_tangent_apply(mesh.handle, _dtype_of(v), up, _dev(v, mesh.n_dofs, "v"), _dev(y, mesh.n_dofs, "y")))
+    check(lib().pfem_tangent_apply(mesh.handle, _dtype_of(v, arith), up, _dev(v, mesh.n_dofs, "v"), _dev(y, mesh.n_dofs, "y")))
     return y
 
 
-def pfem_jacobi_diag(mesh, u=None, d=None, dtype=torch.float32):
+def pfem_jacobi_diag(mesh, u=None, d=None, dtype=torch.float32, arith=None):
     if d is None:
         d = torch.empty(mesh.n_dofs, dtype=u.dtype if u is not None else dtype, device="cuda")
     up = _dev(u, mesh.n_dofs, "u") if u is not None else None
-    check(lib().pfem_jacobi_diag(mesh.handle, _dtype_of(d), up, _dev(d, mesh.n_dofs, "d")))
+    check(lib().pfem_jacobi_diag(mesh.handle, _dtype_of(d, arith), up, _dev(d, mesh.n_dofs, "d")))
     return d
 
 

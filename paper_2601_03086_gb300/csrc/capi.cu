@@ -247,12 +247,16 @@ pfem_status pfem_mesh_set_load_scale(pfem_mesh_t m, double s) {
 static pfem_status op_common(pfem_mesh_t m, pfem_dtype dt) {
   pfem_status st = check_mesh(m);
   if (st) return st;
-  if (dt != PFEM_F32 && dt != PFEM_F64) {
+  if (dt != PFEM_F32 && dt != PFEM_F64 && dt != PFEM_F64_F32) {
     set_error("unknown dtype %d", (int)dt);
     return PFEM_ERR_INVALID_ARG;
   }
   return PFEM_OK;
 }
+
+// vector type / element arithmetic of a dtype
+static pfem_dtype vt_of(pfem_dtype d) { return d == PFEM_F32 ? PFEM_F32 : PFEM_F64; }
+static pfem_dtype ct_of(pfem_dtype d) { return d == PFEM_F64 ? PFEM_F64 : PFEM_F32; }
 
 pfem_status pfem_energy(pfem_mesh_t m, pfem_dtype dt, const void* u, double* energy, double* strain_energy) {
   pfem_status st = op_common(m, dt);
@@ -263,8 +267,8 @@ pfem_status pfem_energy(pfem_mesh_t m, pfem_dtype dt, const void* u, double* ene
   }
   OpArgs a{u, nullptr, nullptr, nullptr, nullptr, m->load_scale};
   PFEM_CUDA(cudaMemsetAsync(m->plan.inverted, 0, sizeof(int32_t), m->stream));
-  if ((st = launch_element_op(m->plan, OP_ENERGY, dt, dt, a, m->stream))) return st;
-  if ((st = launch_energy_finalize(m->plan, dt, u, m->load_scale, m->red_partials, m->red_counter, m->red_out,
+  if ((st = launch_element_op(m->plan, OP_ENERGY, vt_of(dt), ct_of(dt), a, m->stream))) return st;
+  if ((st = launch_energy_finalize(m->plan, vt_of(dt), u, m->load_scale, m->red_partials, m->red_counter, m->red_out,
                                    m->stream)))
     return st;
   PFEM_CUDA(cudaMemcpyAsync(m->host_out, m->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, m->stream));
@@ -287,7 +291,7 @@ pfem_status pfem_residual(pfem_mesh_t m, pfem_dtype dt, const void* u, void* r) 
     return PFEM_ERR_INVALID_ARG;
   }
   OpArgs a{u, nullptr, nullptr, r, nullptr, m->load_scale};
-  return launch_element_op(m->plan, OP_RESIDUAL, dt, dt, a, m->stream);
+  return launch_element_op(m->plan, OP_RESIDUAL, vt_of(dt), ct_of(dt), a, m->stream);
 }
 
 pfem_status pfem_tangent_apply(pfem_mesh_t m, pfem_dtype dt, const void* u, const void* v, void* y) {
@@ -298,7 +302,7 @@ pfem_status pfem_tangent_apply(pfem_mesh_t m, pfem_dtype dt, const void* u, cons
     return PFEM_ERR_INVALID_ARG;
   }
   OpArgs a{u, v, y, nullptr, nullptr, m->load_scale};
-  return launch_element_op(m->plan, OP_TANGENT, dt, dt, a, m->stream);
+  return launch_element_op(m->plan, OP_TANGENT, vt_of(dt), ct_of(dt), a, m->stream);
 }
 
 pfem_status pfem_jacobi_diag(pfem_mesh_t m, pfem_dtype dt, const void* u, void* d) {
@@ -309,7 +313,7 @@ pfem_status pfem_jacobi_diag(pfem_mesh_t m, pfem_dtype dt, const void* u, void* 
     return PFEM_ERR_INVALID_ARG;
   }
   OpArgs a{u, nullptr, nullptr, nullptr, d, m->load_scale};
-  return launch_element_op(m->plan, OP_DIAG, dt, dt, a, m->stream);
+  return launch_element_op(m->plan, OP_DIAG, vt_of(dt), ct_of(dt), a, m->stream);
 }
 
 }  // extern "C"
