@@ -1,6 +1,7 @@
 // C ABI: mesh lifetime and the element-operator entry points (see include/pfem.h).
 
 #include <cstring>
+#include <cstdlib>
 #include <new>
 
 #include "kernels_vec.cuh"
@@ -55,7 +56,9 @@ pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem
   *out = nullptr;
   HostPlan hp;
   std::vector<double> fext;
-  pfem_status st = build_plan(desc, &hp, &fext);
+  int tile_elems = 0;  // 0: size-dependent default; PFEM_TILE_ELEMS overrides (experiments)
+  if (const char* env = std::getenv("PFEM_TILE_ELEMS")) tile_elems = std::atoi(env);
+  pfem_status st = build_plan(desc, &hp, &fext, tile_elems);
   if (st != PFEM_OK) return st;
   const int dim = hp.dim;
   const int64_t nd = hp.n_nodes * dim;
@@ -85,7 +88,9 @@ pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem
   const size_t o_hi = ab.take(hp.halo_info.size() * 4);
   const size_t o_hp = ab.take(hp.halo_ptr.size() * 4);
   const size_t o_hs = ab.take(hp.halo_src.size() * 4);
-  const size_t o_pa = ab.take((size_t)std::max<int64_t>(hp.n_partials, 1) * dim * sizeof(double) * 2);
+  const size_t o_ph = ab.take(hp.partial_halo.size() * 4);
+  const size_t o_hc = ab.take((size_t)std::max<int64_t>(hp.n_halo(), 1) * kMaxRegions * sizeof(int32_t));
+  const size_t o_pa = ab.take((size_t)std::max<int64_t>(hp.n_partials, 1) * 4 * sizeof(double) * kMaxRegions);
   const size_t o_te = ab.take((size_t)std::max<int64_t>(nt, 1) * sizeof(double));
   const size_t o_inv = ab.take(16);
   const size_t o_fe = ab.take((size_t)nd * 8);
@@ -130,10 +135,13 @@ pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem
       (st = upload(base, o_so, hp.slot_off, s)) || (st = upload(base, o_ec, hp.ecode, s)) ||
       (st = upload(base, o_mf, hp.emat_f, s)) || (st = upload(base, o_md, hp.emat_d, s)) ||
       (st = upload(base, o_hi, hp.halo_info, s)) || (st = upload(base, o_hp, hp.halo_ptr, s)) ||
-      (st = upload(base, o_hs, hp.halo_src, s)) || (st = upload(base, o_fe, fext, s)) ||
+      (st = upload(base, o_hs, hp.halo_src, s)) || (st = upload(base, o_ph, hp.partial_halo, s)) ||
+      (st = upload(base, o_fe, fext, s)) ||
       (st = upload(base, o_ff, fext_f, s)) || (st = upload(base, o_dv, vals, s)) || (st = upload(base, o_dm, mask, s)))
     return fail(st);
   ce = cudaMemsetAsync(base + o_inv, 0, 16, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemsetAsync(base + o_hc, 0, (size_t)std::max<int64_t>(hp.n_halo(), 1) * kMaxRegions * sizeof(int32_t), s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(base + o_rc, 0, 64, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);  // host vectors die at return
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "mesh upload"));
@@ -158,6 +166,8 @@ pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem
   P.halo_info = reinterpret_cast<const int32_t*>(base + o_hi);
   P.halo_ptr = reinterpret_cast<const int32_t*>(base + o_hp);
   P.halo_src = reinterpret_cast<const int32_t*>(base + o_hs);
+  P.partial_halo = reinterpret_cast<const int32_t*>(base + o_ph);
+  P.halo_count = reinterpret_cast<int32_t*>(base + o_hc);
   P.partial = base + o_pa;
   P.tile_energy = reinterpret_cast<double*>(base + o_te);
   P.inverted = reinterpret_cast<int32_t*>(base + o_inv);

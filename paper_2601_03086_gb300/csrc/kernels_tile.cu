@@ -1,14 +1,17 @@
-// Element-tile kernels: one CTA per tile, shared-memory staging of the tile's nodes,
-// one thread per element (strided), per-incidence slots, fixed-order node sums.
+// Element-tile kernel: one CTA per tile, shared-memory staging of the tile's nodes, one
+// thread per element (strided), per-incidence slots, fixed-order node sums, and halo nodes
+// finished in-kernel by the last tile to publish its partial.
 //
 // Passes of one tile CTA (every requested output op runs its own element and node pass;
 // element quantities are recomputed, never stored):
 //   stage : tile node coordinates (tile-relative, FP32 or FP64) + u and/or v gathered by id
 //   elem  : per element geometry, kinematics, stress / stress derivative, V * T dN_a into
 //           slot (node, rank); optional V * Psi accumulated per thread
-//   node  : each tile node sums its slots in rank order; complete nodes write the output,
-//           halo nodes write a partial for the halo pass
-// Halo pass: one thread per halo node sums its partials in ascending tile order.
+//   node  : each tile node sums its slots in rank order; a complete node writes its output;
+//           a halo node publishes a partial, and the tile whose partial completes the set
+//           (integer ticket per halo node) sums all partials of that node in ascending tile
+//           order and writes the output. The summation order never depends on timing, so the
+//           result is bitwise reproducible; the ticket is reset by that last tile.
 //
 // Output conventions (Dirichlet DOFs eliminated): tangent y = v on prescribed DOFs and v is
 // read as 0 there; residual r = 0 on prescribed DOFs; diagonal d = 1 on prescribed DOFs.
@@ -26,14 +29,14 @@ struct SmemLayout {
   size_t slot, x, u, v, off, info, red, total;
 };
 
+// Shared memory: 4-wide (x, y, z, pad) records for slots and staged node data.
 template <typename CT>
-__host__ __device__ inline SmemLayout<CT> smem_layout(int dim, int max_local, int slot_cap, bool need_u,
-                                                      bool need_v) {
+__host__ __device__ inline SmemLayout<CT> smem_layout(int max_local, int slot_cap, bool need_u, bool need_v) {
   SmemLayout<CT> L;
   size_t o = 0;
-  auto al = [](size_t x) { return (x + 15) & ~size_t(15); };
+  auto al = [](size_t x) { return (x + 31) & ~size_t(31); };
   L.slot = o;
-  o = al(o + (size_t)dim * slot_cap * sizeof(CT));
+  o = al(o + (size_t)slot_cap * 4 * sizeof(CT));
   L.x = o;
   o = al(o + (size_t)max_local * 4 * sizeof(CT));
   L.u = o;
@@ -50,6 +53,33 @@ __host__ __device__ inline SmemLayout<CT> smem_layout(int dim, int max_local, in
   return L;
 }
 
+// 4-wide loads/stores of compute-type records
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  o[0] = t.x, o[1] = t.y, o[2] = t.z, o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+__device__ __forceinline__ void ldcg4(const float* p, float (&o)[4]) {
+  const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+  o[0] = t.x, o[1] = t.y, o[2] = t.z, o[3] = t.w;
+}
+__device__ __forceinline__ void ldcg4(const double* p, double (&o)[4]) {
+  const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+
 template <typename CT>
 __device__ __forceinline__ const CT* fext_ptr(const DevPlan& P);
 template <>
@@ -57,9 +87,15 @@ __device__ __forceinline__ const float* fext_ptr<float>(const DevPlan& P) { retu
 template <>
 __device__ __forceinline__ const double* fext_ptr<double>(const DevPlan& P) { return P.f_ext; }
 
-template <int DIM, int OUT, typename VT, typename CT>
+// PCG direction of one DOF: p = dinv r + beta p_old (0 on prescribed DOFs)
+__device__ __forceinline__ double pcg_direction(const PcgArgs& g, const double* p_old, double beta, int64_t k,
+                                                bool fixed) {
+  return fixed ? 0.0 : fma(g.dinv[k], g.r[k], beta * p_old[k]);
+}
+
+template <int DIM, int OUT, typename VT, typename CT, bool PCG = false>
 __device__ __forceinline__ void final_write(const DevPlan& P, const OpArgs& A, int64_t gid, unsigned mask,
-                                            const CT (&acc)[DIM]) {
+                                            const CT (&acc)[4]) {
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
     const int64_t k = gid * DIM + i;
@@ -67,6 +103,8 @@ __device__ __forceinline__ void final_write(const DevPlan& P, const OpArgs& A, i
     if (OUT == OUT_RES) {
       const CT f = fext_ptr<CT>(P)[k];
       static_cast<VT*>(A.r)[k] = fixed ? VT(0) : VT(acc[i] - CT(A.load_scale) * f);
+    } else if (OUT == OUT_TAN && PCG) {
+      static_cast<VT*>(A.y)[k] = fixed ? VT(0) : VT(acc[i]);  // directions vanish on prescribed DOFs
     } else if (OUT == OUT_TAN) {
       static_cast<VT*>(A.y)[k] = fixed ? static_cast<const VT*>(A.v)[k] : VT(acc[i]);
     } else {
@@ -75,17 +113,22 @@ __device__ __forceinline__ void final_write(const DevPlan& P, const OpArgs& A, i
   }
 }
 
+// v_e . y_e over the corners of one element (the element's share of v . A v)
 template <int DIM, typename CT>
-__device__ __forceinline__ void load_corner(const unsigned char* smem, const SmemLayout<CT>& L, int l, CT (&x)[3]) {
-  const CT* s = reinterpret_cast<const CT*>(smem + L.x) + 4 * l;
+__device__ __forceinline__ double corner_dot(const CT (&w)[DIM + 1][3], const CT (&out)[DIM + 1][DIM]) {
+  CT s = CT(0);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) x[i] = s[i];
+  for (int a = 0; a <= DIM; ++a)
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) s = fma(w[a][i], out[a][i], s);
+  return (double)s;
 }
 
-// One element pass for output OUT (or energy only when OUT < 0).
-template <int DIM, int KIND, int OUT, bool ENERGY, bool COUNT, typename VT, typename CT>
+// One element pass for output OUT (or energy only when OUT < 0). PAP: accumulate v . A_e v
+// into e_acc (tangent pass of the PCG-fused apply).
+template <int DIM, int KIND, int OUT, bool ENERGY, bool COUNT, typename CT, bool PAP = false>
 __device__ __forceinline__ void element_pass(const DevPlan& P, unsigned char* smem, const SmemLayout<CT>& L, int ebeg,
-                                             int ne, int slot_cap, double& e_acc, int& n_inv) {
+                                             int ne, double& e_acc, int& n_inv) {
   constexpr int NV = DIM + 1;
   const CT* sx = reinterpret_cast<const CT*>(smem + L.x);
   const CT* su = reinterpret_cast<const CT*>(smem + L.u);
@@ -106,16 +149,21 @@ __device__ __forceinline__ void element_pass(const DevPlan& P, unsigned char* sm
       lam = m.y;
     }
     int loc[NV];
-    CT X[NV][3];
+    CT X[NV][4];
 #pragma unroll
     for (int a = 0; a < NV; ++a) {
       loc[a] = cs[a] & 1023;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) X[a][i] = sx[4 * loc[a] + i];
+      ld4(sx + 4 * loc[a], X[a]);
     }
     ElemGeo<DIM, CT> G;
-    if constexpr (DIM == 3) geometry3<CT>(X, G);
-    else {
+    if constexpr (DIM == 3) {
+      CT X3[4][3];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) X3[a][i] = X[a][i];
+      geometry3<CT>(X3, G);
+    } else {
       CT X2[3][3];
 #pragma unroll
       for (int a = 0; a < 3; ++a)
@@ -128,9 +176,11 @@ __device__ __forceinline__ void element_pass(const DevPlan& P, unsigned char* sm
     if constexpr (NEED_GU) {
       CT w[NV][3];
 #pragma unroll
-      for (int a = 0; a < NV; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) w[a][i] = su[4 * loc[a] + i];
+      for (int a = 0; a < NV; ++a) {
+        CT t[4];
+        ld4(su + 4 * loc[a], t);
+        w[a][0] = t[0], w[a][1] = t[1], w[a][2] = t[2];
+      }
       grad_of<DIM, CT>(G, w, Gu);
     }
     CT out[NV][DIM];
@@ -143,13 +193,16 @@ __device__ __forceinline__ void element_pass(const DevPlan& P, unsigned char* sm
       } else if constexpr (OUT == OUT_TAN) {
         CT w[NV][3];
 #pragma unroll
-        for (int a = 0; a < NV; ++a)
-#pragma unroll
-          for (int i = 0; i < 3; ++i) w[a][i] = sv[4 * loc[a] + i];
+        for (int a = 0; a < NV; ++a) {
+          CT t[4];
+          ld4(sv + 4 * loc[a], t);
+          w[a][0] = t[0], w[a][1] = t[1], w[a][2] = t[2];
+        }
         CT Gv[DIM][DIM], S[DIM][DIM];
         grad_of<DIM, CT>(G, w, Gv);
         linear_stress<DIM, CT>(Gv, mu, lam, S);
         contract<DIM, CT>(G, S, out);
+        if constexpr (PAP) e_acc += corner_dot<DIM, CT>(w, out);
       } else if constexpr (OUT == OUT_DIAG) {
         nh_diag<DIM, CT>(G, static_cast<const NHState<DIM, CT>*>(nullptr), mu, lam, out);
       }
@@ -168,13 +221,16 @@ __device__ __forceinline__ void element_pass(const DevPlan& P, unsigned char* sm
       } else if constexpr (OUT == OUT_TAN) {
         CT w[NV][3];
 #pragma unroll
-        for (int a = 0; a < NV; ++a)
-#pragma unroll
-          for (int i = 0; i < 3; ++i) w[a][i] = sv[4 * loc[a] + i];
+        for (int a = 0; a < NV; ++a) {
+          CT t[4];
+          ld4(sv + 4 * loc[a], t);
+          w[a][0] = t[0], w[a][1] = t[1], w[a][2] = t[2];
+        }
         CT Gv[DIM][DIM], dP[DIM][DIM];
         grad_of<DIM, CT>(G, w, Gv);
         nh_dpk1<DIM, CT>(s, mu, lam, Gv, dP);
         contract<DIM, CT>(G, dP, out);
+        if constexpr (PAP) e_acc += corner_dot<DIM, CT>(w, out);
       } else if constexpr (OUT == OUT_DIAG) {
         nh_diag<DIM, CT>(G, &s, mu, lam, out);
       }
@@ -183,53 +239,89 @@ __device__ __forceinline__ void element_pass(const DevPlan& P, unsigned char* sm
 #pragma unroll
       for (int a = 0; a < NV; ++a) {
         const int sl = soff[loc[a]] + (cs[a] >> 10);
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) slot[i * slot_cap + sl] = out[a][i];
+        st4(slot + 4 * sl, out[a][0], out[a][1], DIM == 3 ? out[a][DIM - 1] : CT(0), CT(0));
       }
     }
   }
 }
 
-template <int DIM, int OUT, typename VT, typename CT>
+template <int DIM, int OUT, typename VT, typename CT, bool PCG = false>
 __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, unsigned char* smem,
-                                          const SmemLayout<CT>& L, int nl, int ncomp, int pbeg, int slot_cap,
-                                          int region) {
+                                          const SmemLayout<CT>& L, int nl, int ncomp, int pbeg, int region,
+                                          const double* p_old = nullptr, double* p_new = nullptr, double beta = 0.0) {
   const int* soff = reinterpret_cast<const int*>(smem + L.off);
   const int* sinfo = reinterpret_cast<const int*>(smem + L.info);
   const CT* slot = reinterpret_cast<const CT*>(smem + L.slot);
-  CT* part = static_cast<CT*>(P.partial) + (size_t)region * P.n_partials * DIM;
+  CT* part = static_cast<CT*>(P.partial) + (size_t)region * P.n_partials * 4;
+  int32_t* count = P.halo_count + (size_t)region * P.n_halo;
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     const int b = soff[l], e = soff[l + 1];
-    CT acc[DIM];
+    CT acc[4] = {CT(0), CT(0), CT(0), CT(0)};
+    for (int k = b; k < e; ++k) {
+      CT t[4];
+      ld4(slot + 4 * k, t);
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) acc[i] = CT(0);
-    for (int k = b; k < e; ++k)
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) acc[i] += slot[i * slot_cap + k];
-    const unsigned info = (unsigned)sinfo[l];
+      for (int i = 0; i < DIM; ++i) acc[i] += t[i];
+    }
     if (l < ncomp) {
-      final_write<DIM, OUT, VT, CT>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, acc);
-    } else {
-      const int64_t pi = (int64_t)(pbeg + l - ncomp) * DIM;
+      const unsigned info = (unsigned)sinfo[l];
+      final_write<DIM, OUT, VT, CT, PCG>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, acc);
+      continue;
+    }
+    // halo node: publish this tile's partial, the tile completing the set finishes the node
+    const int pi = pbeg + l - ncomp;
+    st4(part + 4 * (size_t)pi, acc[0], acc[1], acc[2], CT(0));
+    __threadfence();
+    const int h = P.partial_halo[pi];
+    const int pb = P.halo_ptr[h], pe = P.halo_ptr[h + 1];
+    if (atomicAdd(count + h, 1) == pe - pb - 1) {
+      __threadfence();
+      CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
+      for (int k = pb; k < pe; ++k) {
+        CT t[4];
+        ldcg4(part + 4 * (size_t)P.halo_src[k], t);
 #pragma unroll
-      for (int i = 0; i < DIM; ++i) part[pi + i] = acc[i];
+        for (int i = 0; i < DIM; ++i) sum[i] += t[i];
+      }
+      const unsigned hinfo = (unsigned)P.halo_info[h];
+      const int64_t hgid = (int64_t)(hinfo & kInfoIdMask);
+      if constexpr (PCG) {  // the node's new direction, as every tile staged it
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          const int64_t k = hgid * DIM + i;
+          p_new[k] = pcg_direction(A.pcg, p_old, beta, k, ((hinfo >> kInfoIdBits) >> i) & 1u);
+        }
+      }
+      final_write<DIM, OUT, VT, CT, PCG>(P, A, hgid, hinfo >> kInfoIdBits, sum);
+      count[h] = 0;
     }
   }
 }
 
 template <int DIM, int KIND, int OPS, typename VT, typename CT>
 __global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(32) unsigned char smem[];
   constexpr int NV = DIM + 1;
   constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
-  const SmemLayout<CT> L = smem_layout<CT>(DIM, P.max_local, P.slot_cap, NEED_U, NEED_V);
+  const SmemLayout<CT> L = smem_layout<CT>(P.max_local, P.slot_cap, NEED_U, NEED_V);
   const int t = blockIdx.x;
   const int4 ta = P.tile_a[t];
   const int4 tb = P.tile_b[t];
   const int ebeg = ta.x, ne = ta.y, lbeg = ta.z, nl = ta.w;
   const int ncomp = tb.x, pbeg = tb.y;
-  const int slot_cap = P.slot_cap;
+  constexpr bool PCG = (OPS & OP_PCG) != 0;
+  const double* p_old = nullptr;
+  double* p_new = nullptr;
+  double beta = 0.0;
+  if constexpr (PCG) {
+    // the state is written only by earlier kernels, so every CTA takes the same branch
+    const PcgState* st = A.pcg.st;
+    if (st->done != 0 || st->repl != 0) return;
+    beta = st->beta;
+    p_old = A.pcg.p[st->iter & 1];
+    p_new = A.pcg.p[(st->iter + 1) & 1];
+  }
 
   // ---- stage tile nodes
   {
@@ -244,23 +336,36 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
       const float4 rf = P.lnode_f[lbeg + l];
       const int info = __float_as_int(rf.w);
       if constexpr (sizeof(CT) == 4) {
-        sx[4 * l] = rf.x;
-        sx[4 * l + 1] = rf.y;
-        sx[4 * l + 2] = rf.z;
+        st4(sx + 4 * l, rf.x, rf.y, rf.z, 0.f);
       } else {
         const PfemDouble4 rd = P.lnode_d[lbeg + l];
-        sx[4 * l] = rd.x;
-        sx[4 * l + 1] = rd.y;
-        sx[4 * l + 2] = rd.z;
+        st4(sx + 4 * l, rd.x, rd.y, rd.z, 0.0);
       }
       sinfo[l] = info;
       soff[l] = (int)P.slot_off[lbeg + l];
       const int64_t gid = (int64_t)((unsigned)info & kInfoIdMask);
       const unsigned mask = (unsigned)info >> kInfoIdBits;
+      if constexpr (NEED_U) {
+        CT w[3] = {CT(0), CT(0), CT(0)};
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        if constexpr (NEED_U) su[4 * l + i] = i < DIM ? CT(u[gid * DIM + i]) : CT(0);
-        if constexpr (NEED_V) sv[4 * l + i] = (i < DIM && !((mask >> i) & 1u)) ? CT(v[gid * DIM + i]) : CT(0);
+        for (int i = 0; i < DIM; ++i) w[i] = CT(u[gid * DIM + i]);
+        st4(su + 4 * l, w[0], w[1], w[2], CT(0));
+      }
+      if constexpr (PCG) {
+        CT w[3] = {CT(0), CT(0), CT(0)};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          const int64_t k = gid * DIM + i;
+          const double pn = pcg_direction(A.pcg, p_old, beta, k, (mask >> i) & 1u);
+          if (l < ncomp) p_new[k] = pn;  // complete nodes: this tile owns the DOF
+          w[i] = CT(pn);
+        }
+        st4(sv + 4 * l, w[0], w[1], w[2], CT(0));
+      } else if constexpr (NEED_V) {
+        CT w[3] = {CT(0), CT(0), CT(0)};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) w[i] = ((mask >> i) & 1u) ? CT(0) : CT(v[gid * DIM + i]);
+        st4(sv + 4 * l, w[0], w[1], w[2], CT(0));
       }
     }
     if (threadIdx.x == 0) soff[nl] = ne * NV;
@@ -271,32 +376,32 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
   int n_inv = 0;
   int region = 0;
   if constexpr ((OPS & OP_RESIDUAL) != 0) {
-    element_pass<DIM, KIND, OUT_RES, (OPS & OP_ENERGY) != 0, true, VT, CT>(P, smem, L, ebeg, ne, slot_cap, e_acc,
-                                                                         n_inv);
+    element_pass<DIM, KIND, OUT_RES, (OPS & OP_ENERGY) != 0, true, CT>(P, smem, L, ebeg, ne, e_acc, n_inv);
     __syncthreads();
-    node_pass<DIM, OUT_RES, VT, CT>(P, A, smem, L, nl, ncomp, pbeg, slot_cap, region++);
+    node_pass<DIM, OUT_RES, VT, CT>(P, A, smem, L, nl, ncomp, pbeg, region++);
     __syncthreads();
   } else if constexpr ((OPS & OP_ENERGY) != 0) {
-    element_pass<DIM, KIND, -1, true, true, VT, CT>(P, smem, L, ebeg, ne, slot_cap, e_acc, n_inv);
+    element_pass<DIM, KIND, -1, true, true, CT>(P, smem, L, ebeg, ne, e_acc, n_inv);
   }
   if constexpr ((OPS & OP_TANGENT) != 0) {
-    element_pass<DIM, KIND, OUT_TAN, false, (OPS & (OP_RESIDUAL | OP_ENERGY)) == 0, VT, CT>(P, smem, L, ebeg, ne,
-                                                                                         slot_cap, e_acc, n_inv);
+    element_pass<DIM, KIND, OUT_TAN, false, (OPS & (OP_RESIDUAL | OP_ENERGY)) == 0, CT, PCG>(P, smem, L, ebeg, ne,
+                                                                                          e_acc, n_inv);
     __syncthreads();
-    node_pass<DIM, OUT_TAN, VT, CT>(P, A, smem, L, nl, ncomp, pbeg, slot_cap, region++);
+    node_pass<DIM, OUT_TAN, VT, CT, PCG>(P, A, smem, L, nl, ncomp, pbeg, region++, p_old, p_new, beta);
     __syncthreads();
   }
   if constexpr ((OPS & OP_DIAG) != 0) {
-    element_pass<DIM, KIND, OUT_DIAG, false, (OPS & (OP_RESIDUAL | OP_ENERGY | OP_TANGENT)) == 0, VT, CT>(
-        P, smem, L, ebeg, ne, slot_cap, e_acc, n_inv);
+    element_pass<DIM, KIND, OUT_DIAG, false, (OPS & (OP_RESIDUAL | OP_ENERGY | OP_TANGENT)) == 0, CT>(
+        P, smem, L, ebeg, ne, e_acc, n_inv);
     __syncthreads();
-    node_pass<DIM, OUT_DIAG, VT, CT>(P, A, smem, L, nl, ncomp, pbeg, slot_cap, region++);
+    node_pass<DIM, OUT_DIAG, VT, CT>(P, A, smem, L, nl, ncomp, pbeg, region++);
   }
   if constexpr (KIND == K_NH) {
     const int tot = __reduce_add_sync(0xffffffffu, n_inv);
     if ((threadIdx.x & 31) == 0 && tot > 0 && P.inverted) atomicAdd(P.inverted, tot);
   }
-  if constexpr ((OPS & OP_ENERGY) != 0) {
+  if constexpr ((OPS & OP_ENERGY) != 0 || PCG) {
+    // tile sum of the energy (or of p_e . A_e p_e): warp butterflies, warps in index order
     double* red = reinterpret_cast<double*>(smem + L.red);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
@@ -306,44 +411,42 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
     if (threadIdx.x == 0) {
       double s = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-      P.tile_energy[t] = s;
+      if constexpr (PCG) A.pcg.tile_part[t] = s;
+      else P.tile_energy[t] = s;
     }
   }
-}
-
-template <int DIM, int OPS, typename VT, typename CT>
-__global__ void __launch_bounds__(256) halo_kernel(DevPlan P, OpArgs A) {
-  const int h = blockIdx.x * blockDim.x + threadIdx.x;
-  if (h >= P.n_halo) return;
-  const unsigned info = (unsigned)P.halo_info[h];
-  const int64_t gid = (int64_t)(info & kInfoIdMask);
-  const unsigned mask = info >> kInfoIdBits;
-  const int b = P.halo_ptr[h], e = P.halo_ptr[h + 1];
-  int region = 0;
-  auto sum = [&](int reg, CT (&acc)[DIM]) {
-    const CT* part = static_cast<const CT*>(P.partial) + (size_t)reg * P.n_partials * DIM;
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) acc[i] = CT(0);
-    for (int k = b; k < e; ++k) {
-      const int64_t s = (int64_t)P.halo_src[k] * DIM;
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) acc[i] += part[s + i];
+  if constexpr (PCG) {
+    // the last tile to finish sums the tile partials in tile order: alpha = rho / (p . A p)
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(A.pcg.ticket, 1u) == gridDim.x - 1;
     }
-  };
-  if constexpr ((OPS & OP_RESIDUAL) != 0) {
-    CT acc[DIM];
-    sum(region++, acc);
-    final_write<DIM, OUT_RES, VT, CT>(P, A, gid, mask, acc);
-  }
-  if constexpr ((OPS & OP_TANGENT) != 0) {
-    CT acc[DIM];
-    sum(region++, acc);
-    final_write<DIM, OUT_TAN, VT, CT>(P, A, gid, mask, acc);
-  }
-  if constexpr ((OPS & OP_DIAG) != 0) {
-    CT acc[DIM];
-    sum(region++, acc);
-    final_write<DIM, OUT_DIAG, VT, CT>(P, A, gid, mask, acc);
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      double s = 0.0;
+      for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(A.pcg.tile_part + i);
+      double* red = reinterpret_cast<double*>(smem + L.red);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double pap = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pap += red[w];
+        PcgState* st = A.pcg.st;
+        // negative curvature does not stop plain CG; p.Ap = 0 or non-finite does
+        if (pap == 0.0 || !isfinite(pap)) {
+          st->alpha = 0.0;
+          st->done = isfinite(pap) ? PCG_BREAKDOWN : PCG_NONFINITE;
+        } else {
+          st->alpha = st->rho / pap;
+        }
+        *A.pcg.ticket = 0u;
+      }
+    }
   }
 }
 
@@ -351,28 +454,21 @@ template <int DIM, int KIND, int OPS, typename VT, typename CT>
 static pfem_status run(const DevPlan& P, const OpArgs& A, cudaStream_t s) {
   constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
-  const SmemLayout<CT> L = smem_layout<CT>(DIM, P.max_local, P.slot_cap, NEED_U, NEED_V);
-  if (P.n_tiles > 0) {
-    static int attr_done = 0;  // per instantiation; allow the full 227 KB once
-    if (!attr_done) {
-      PFEM_CUDA(cudaFuncSetAttribute(tile_kernel<DIM, KIND, OPS, VT, CT>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-      attr_done = 1;
-    }
-    if (L.total > 227 * 1024) {
-      set_error("tile needs %zu bytes of shared memory", L.total);
-      return PFEM_ERR_UNSUPPORTED;
-    }
-    tile_kernel<DIM, KIND, OPS, VT, CT><<<P.n_tiles, kThreads, L.total, s>>>(P, A); PFEM_COUNT_LAUNCH();
-    PFEM_CUDA(cudaGetLastError());
+  const SmemLayout<CT> L = smem_layout<CT>(P.max_local, P.slot_cap, NEED_U, NEED_V);
+  if (P.n_tiles <= 0) return PFEM_OK;
+  static int attr_done = 0;  // per instantiation; allow the full 227 KB once
+  if (!attr_done) {
+    PFEM_CUDA(cudaFuncSetAttribute(tile_kernel<DIM, KIND, OPS, VT, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   227 * 1024));
+    attr_done = 1;
   }
-  constexpr int HOPS = OPS & (OP_RESIDUAL | OP_TANGENT | OP_DIAG);
-  if constexpr (HOPS != 0) {
-    if (P.n_halo > 0) {
-      halo_kernel<DIM, HOPS, VT, CT><<<(P.n_halo + 255) / 256, 256, 0, s>>>(P, A); PFEM_COUNT_LAUNCH();
-      PFEM_CUDA(cudaGetLastError());
-    }
+  if (L.total > 227 * 1024) {
+    set_error("tile needs %zu bytes of shared memory", L.total);
+    return PFEM_ERR_UNSUPPORTED;
   }
+  tile_kernel<DIM, KIND, OPS, VT, CT><<<P.n_tiles, kThreads, L.total, s>>>(P, A);
+  PFEM_COUNT_LAUNCH();
+  PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
 
@@ -383,6 +479,9 @@ static pfem_status dispatch_ops(const DevPlan& P, int ops, const OpArgs& A, cuda
     case OP_RESIDUAL: return run<DIM, KIND, OP_RESIDUAL, VT, CT>(P, A, s);
     case OP_ENERGY: return run<DIM, KIND, OP_ENERGY, VT, CT>(P, A, s);
     case OP_DIAG: return run<DIM, KIND, OP_DIAG, VT, CT>(P, A, s);
+    case OP_TANGENT | OP_PCG:
+      if constexpr (sizeof(VT) == 8) return run<DIM, KIND, OP_TANGENT | OP_PCG, VT, CT>(P, A, s);
+      break;
     default: break;
   }
   set_error("unsupported op combination %d", ops);
@@ -411,8 +510,8 @@ pfem_status launch_element_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dty
 size_t element_op_smem(const DevPlan& P, int ops, pfem_dtype ct) {
   const bool need_u = (ops & (OP_RESIDUAL | OP_ENERGY)) || (P.kind == PFEM_NEOHOOKEAN && (ops & (OP_TANGENT | OP_DIAG)));
   const bool need_v = (ops & OP_TANGENT) != 0;
-  if (ct == PFEM_F32) return smem_layout<float>(P.dim, P.max_local, P.slot_cap, need_u, need_v).total;
-  return smem_layout<double>(P.dim, P.max_local, P.slot_cap, need_u, need_v).total;
+  if (ct == PFEM_F32) return smem_layout<float>(P.max_local, P.slot_cap, need_u, need_v).total;
+  return smem_layout<double>(P.max_local, P.slot_cap, need_u, need_v).total;
 }
 
 }  // namespace pfem

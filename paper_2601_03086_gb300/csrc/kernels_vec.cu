@@ -77,12 +77,18 @@ __global__ void __launch_bounds__(kReduceThreads)
 }
 
 // x += alpha p; r -= alpha q; (r.z, r.r) with z = dinv r; flags and beta in the last block.
+// p is this iteration's direction, p_buf[(iter + 1) & 1] (written by the fused apply).
 __global__ void __launch_bounds__(kReduceThreads)
-    pcg_update_kernel(int64_t n, double* x, double* r, const double* p, const double* q, const double* dinv,
-                      PcgState* st, double* partials, unsigned int* counter, cudaGraphConditionalHandle cond,
-                      int set_cond) {
+    pcg_update_kernel(int64_t n, double* x, double* r, const double* p0, const double* p1, const double* q,
+                      const double* dinv, PcgState* st, double* partials, unsigned int* counter,
+                      cudaGraphConditionalHandle cond, int set_cond) {
   __shared__ double scratch[16];
+  if (st->done != 0 || st->repl != 0) {  // nothing to do (uniform: written by earlier kernels)
+    if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    return;
+  }
   const double alpha = st->alpha;
+  const double* p = ((st->iter + 1) & 1) ? p1 : p0;
   double v[2] = {0.0, 0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     x[i] += alpha * p[i];
@@ -201,11 +207,12 @@ pfem_status vk_alpha(int64_t n, const double* p, const double* q, PcgState* st, 
   return PFEM_OK;
 }
 
-pfem_status vk_update(int64_t n, double* x, double* r, const double* p, const double* q, const double* dinv,
-                      PcgState* st, double* partials, unsigned int* counter, cudaGraphConditionalHandle cond,
-                      int set_cond, cudaStream_t s) {
-  pcg_update_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, x, r, p, q, dinv, st, partials, counter, cond,
-                                                            set_cond); PFEM_COUNT_LAUNCH();
+pfem_status vk_update(int64_t n, double* x, double* r, const double* p0, const double* p1, const double* q,
+                      const double* dinv, PcgState* st, double* partials, unsigned int* counter,
+                      cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s) {
+  pcg_update_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, x, r, p0, p1, q, dinv, st, partials, counter, cond,
+                                                            set_cond);
+  PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }

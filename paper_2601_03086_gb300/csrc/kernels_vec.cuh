@@ -7,34 +7,14 @@
 
 namespace pfem {
 
-enum : int { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_MAXITER = 2, PCG_NONFINITE = 3, PCG_BREAKDOWN = 4 };
-
-// Device-resident scalars of one Jacobi-PCG solve (FP64).
-struct PcgState {
-  double rho;             // r . z of the current residual
-  double alpha, beta;
-  double rel;             // latest relative residual (recursive, or true right after a replacement)
-  double rel_true;        // latest FP64 true relative residual
-  double ref;             // reference norm of the stopping rule
-  double tol;
-  double repl_threshold;  // a recursive residual below this triggers an FP64 replacement
-  double repl_factor;     // next threshold = factor * true residual at the last replacement
-  int iter;
-  int max_iter;
-  int done;               // PCG_* code, 0 while running
-  int repl;               // 1 = stop the device loop for an FP64 residual replacement
-  int replacements;
-  int pad;
-};
-
 pfem_status vk_lift(int64_t n, const double* u0, const double* values, const uint8_t* mask, double s, double* x,
                     cudaStream_t st);
 pfem_status vk_invert_diag(int64_t n, const void* d, pfem_dtype dt, double* dinv, cudaStream_t st);
 pfem_status vk_alpha(int64_t n, const double* p, const double* q, PcgState* st, double* partials,
                      unsigned int* counter, cudaStream_t s);
-pfem_status vk_update(int64_t n, double* x, double* r, const double* p, const double* q, const double* dinv,
-                      PcgState* st, double* partials, unsigned int* counter, cudaGraphConditionalHandle cond,
-                      int set_cond, cudaStream_t s);
+pfem_status vk_update(int64_t n, double* x, double* r, const double* p0, const double* p1, const double* q,
+                      const double* dinv, PcgState* st, double* partials, unsigned int* counter,
+                      cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s);
 pfem_status vk_direction(int64_t n, const double* r, const double* dinv, double* p, const PcgState* st,
                          cudaStream_t s);
 pfem_status vk_replace(int64_t n, const double* res, double* r, const double* dinv, PcgState* st, int restart,

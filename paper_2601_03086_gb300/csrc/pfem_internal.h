@@ -46,6 +46,7 @@ constexpr int kMaxRank = 63;       // max incidences of one node inside one tile
 constexpr int kInfoIdBits = 28;
 constexpr uint32_t kInfoIdMask = (1u << kInfoIdBits) - 1u;
 constexpr int kThreads = 256;      // threads per tile CTA
+constexpr int kMaxRegions = 3;     // output ops one tile launch can produce (partials/tickets each)
 constexpr int kReduceBlocks = 296; // fixed grid of the deterministic FP64 reductions (2 x 148)
 
 // Kernels enqueued by this thread (launches recorded into a graph are counted by the caller
@@ -80,14 +81,18 @@ struct HostPlan {
   std::vector<int32_t> halo_src;  // n_partials
   int64_t n_partials = 0;
   std::vector<int32_t> elem_perm; // original element id at each tile-order position
+  std::vector<int32_t> partial_halo; // halo node index of each partial
   int64_t n_tiles() const { return (int64_t)tile_a.size() / 4; }
   int64_t n_local() const { return (int64_t)slot_off.size(); }
   int64_t n_halo() const { return (int64_t)halo_info.size(); }
 };
 
 // Validates desc and builds the plan plus the FP64 external force. Returns status.
-pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* plan, std::vector<double>* f_ext,
-                       int tile_elems = kTileElems);
+// tile_elems <= 0 or > kTileElems selects default_tile_elems(n_elems).
+pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* plan, std::vector<double>* f_ext, int tile_elems = 0);
+
+// Default elements per tile for a mesh of n_elems elements.
+int default_tile_elems(int64_t n_elems);
 
 // Structural self-check of a plan against its description (host only).
 pfem_status verify_plan(const pfem_mesh_desc* d, const HostPlan& plan);
@@ -113,7 +118,9 @@ struct DevPlan {
   const int32_t* halo_info;
   const int32_t* halo_ptr;
   const int32_t* halo_src;
-  void* partial;         // scratch: n_partials * dim values of the compute type (x2 for fused)
+  const int32_t* partial_halo;  // halo node index of each partial
+  int32_t* halo_count;   // per region x halo node: partials published so far (reset by the last)
+  void* partial;         // scratch: per region n_partials slots of 4 compute-type values
   double* tile_energy;   // per-tile strain-energy partials
   int32_t* inverted;     // count of J <= 0 elements (device int)
   const double* f_ext;   // n_dofs, FP64, at full load
@@ -128,6 +135,40 @@ enum : int {
   OP_RESIDUAL = 2,  // r = P (f_int(u) - s f_ext)
   OP_ENERGY = 4,    // per-tile sum of V Psi
   OP_DIAG = 8,      // d = diag A(u)
+  OP_PCG = 16,      // with OP_TANGENT: PCG-fused apply (direction update + p.Ap + alpha)
+};
+
+enum : int { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_MAXITER = 2, PCG_NONFINITE = 3, PCG_BREAKDOWN = 4 };
+
+// Device-resident scalars of one Jacobi-PCG solve (FP64).
+struct PcgState {
+  double rho;             // r . z of the current residual
+  double alpha, beta;
+  double rel;             // latest relative residual (recursive, or true right after a replacement)
+  double rel_true;        // latest FP64 true relative residual
+  double ref;             // reference norm of the stopping rule
+  double tol;
+  double repl_threshold;  // a recursive residual below this triggers an FP64 replacement
+  double repl_factor;     // next threshold = factor * true residual at the last replacement
+  int iter;               // completed iterations; direction buffers alternate with its parity
+  int max_iter;
+  int done;               // PCG_* code, 0 while running
+  int repl;               // 1 = stop the device loop for an FP64 residual replacement
+  int replacements;
+  int pad;
+};
+
+// Extra inputs of the PCG-fused tangent apply (OP_PCG): the search direction is formed on
+// the fly, p = dinv r + beta p_old, written to p[(iter + 1) & 1], and A p goes to y; each tile
+// also sums p_e . (A_e p_e) over its elements, and the last tile turns the tile sums into
+// alpha = rho / (p . A p).
+struct PcgArgs {
+  const double* r;
+  const double* dinv;
+  double* p[2];           // direction buffers (p_old = p[iter & 1])
+  PcgState* st;
+  double* tile_part;      // n_tiles doubles
+  unsigned int* ticket;   // zero-initialised; reset by the last tile
 };
 
 struct OpArgs {
@@ -137,6 +178,7 @@ struct OpArgs {
   void* r;          // VT* residual output
   void* d;          // VT* diagonal output
   double load_scale;
+  PcgArgs pcg;      // OP_PCG only
 };
 
 // Launches the tile kernel and the halo pass for one mesh (kernels_tile.cu).

@@ -65,6 +65,17 @@ static bool finite_all(const double* p, int64_t n) {
   return true;
 }
 
+// Tile size: 512 elements once the mesh fills the GPU several times over (fewer halo
+// partials per element); smaller tiles for small meshes so that at least ~8 tiles land on
+// each of the 152 SMs (latency hiding beats halo overhead there).
+int default_tile_elems(int64_t n_elems) {
+  const int64_t per = (n_elems + 152 * 8 - 1) / (152 * 8);
+  int64_t t = (per + 63) / 64 * 64;
+  if (t < 128) t = 128;
+  if (t > 512) t = 512;
+  return (int)t;
+}
+
 pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>* f_ext, int tile_elems) {
   if (!d || !P || !f_ext) {
     set_error("null argument");
@@ -93,7 +104,7 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
     set_error("unknown material kind %d", d->kind);
     return PFEM_ERR_INVALID_ARG;
   }
-  if (tile_elems < 1 || tile_elems > kTileElems) tile_elems = kTileElems;
+  if (tile_elems < 1 || tile_elems > kTileElems) tile_elems = default_tile_elems(E);
   const double* X = d->coords;
   if (!finite_all(X, N * dim)) {
     set_error("non-finite coordinate");
@@ -308,8 +319,16 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
     }
   }
   if (E > 0) close_tile(E);
+  // Orphan nodes (no element) go to element-free tiles as complete nodes of degree zero, so
+  // the tile kernel writes their outputs too.
+  for (int64_t n = 0; n < N; ++n) {
+    if (gdeg[(size_t)n] != 0) continue;
+    cur_nodes.push_back((int32_t)n);
+    if ((int)cur_nodes.size() == kTileNodes) close_tile(E);
+  }
+  if (!cur_nodes.empty()) close_tile(E);
 
-  // ---- halo CSR: halo nodes (and orphan nodes with no element) by ascending id ------------
+  // ---- halo CSR: nodes shared by several tiles, by ascending id ---------------------------
   std::vector<int32_t> cnt((size_t)N, 0);
   for (auto& pr : halo_pairs) cnt[pr.first]++;
   P->halo_info.clear();
@@ -317,7 +336,7 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
   std::vector<int32_t> start((size_t)N, -1);
   int64_t acc = 0;
   for (int64_t n = 0; n < N; ++n) {
-    if (cnt[n] > 0 || gdeg[n] == 0) {
+    if (cnt[n] > 0) {
       P->halo_info.push_back(info_of(n));
       start[n] = (int32_t)acc;
       acc += cnt[n];
@@ -328,6 +347,10 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
   std::vector<int32_t> fill((size_t)N, 0);
   for (auto& pr : halo_pairs) P->halo_src[(size_t)(start[pr.first] + fill[pr.first]++)] = pr.second;
   P->n_partials = n_partials;
+  P->partial_halo.assign((size_t)n_partials, 0);
+  for (int64_t h = 0; h < P->n_halo(); ++h)
+    for (int32_t k = P->halo_ptr[(size_t)h]; k < P->halo_ptr[(size_t)h + 1]; ++k)
+      P->partial_halo[(size_t)P->halo_src[(size_t)k]] = (int32_t)h;
 
   // ---- external force ---------------------------------------------------------------------
   f_ext->assign((size_t)(N * dim), 0.0);
@@ -378,7 +401,7 @@ pfem_status verify_plan(const pfem_mesh_desc* d, const HostPlan& P) {
     const int32_t* ta = &P.tile_a[(size_t)t * 4];
     const int32_t* tb = &P.tile_b[(size_t)t * 4];
     const int eb = ta[0], ne = ta[1], lb = ta[2], nl = ta[3], nc = tb[0], pb = tb[1];
-    if (eb != next_e || ne < 1) return bad("tiles must cover elements contiguously", t, eb);
+    if (eb != next_e || ne < 0 || (ne == 0 && eb != E)) return bad("tiles must cover elements contiguously", t, eb);
     next_e = eb + ne;
     if (nl < 1 || nl > kTileNodes || nc > nl) return bad("tile node count", t, nl);
     std::vector<int> seen((size_t)ne * nv, 0), next_rank((size_t)nl, 0);
@@ -438,6 +461,9 @@ pfem_status verify_plan(const pfem_mesh_desc* d, const HostPlan& P) {
       deg += (int)partial_deg_of[(size_t)pi];
     }
     if (deg != gdeg[(size_t)gid]) return bad("halo node incidences", gid, deg);
+    for (int k = b; k < e; ++k)
+      if (P.partial_halo[(size_t)P.halo_src[(size_t)k]] != (int32_t)h) return bad("partial -> halo map", gid, k);
+    if (gdeg[(size_t)gid] == 0) return bad("orphan node in the halo list", gid, h);
   }
   for (int64_t n = 0; n < N; ++n)
     if (owner[(size_t)n] == -1 && !listed[(size_t)n]) return bad("node neither complete nor listed", n, 0);

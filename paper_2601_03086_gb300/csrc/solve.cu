@@ -29,7 +29,9 @@ static int g_solver_mode = 0;  // 0 = device while-loop graph, 1 = plain host lo
 struct SolverWS {
   int64_t n = 0;
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *res = nullptr;
-  double *u = nullptr, *rn = nullptr, *tmp = nullptr;
+  double *u = nullptr, *rn = nullptr, *tmp = nullptr, *p2 = nullptr;
+  double* tile_part = nullptr;       // per-tile p . A p partials of the fused apply
+  unsigned int* ticket = nullptr;    // last-tile ticket of the fused apply
   PcgState* st = nullptr;    // device
   PcgState* hst = nullptr;   // pinned host mirror
   double* dnorm = nullptr;   // device scalar
@@ -75,18 +77,22 @@ static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
   SolverWS* w = new SolverWS();
   w->n = m->n_dofs;
   const size_t vb = ((size_t)w->n * sizeof(double) + 255) & ~size_t(255);
-  w->bytes = 9 * vb + 512;
+  const size_t tb = ((size_t)std::max(m->plan.n_tiles, 1) * sizeof(double) + 255) & ~size_t(255);
+  w->bytes = 10 * vb + tb + 768;
   cudaError_t e = cudaMalloc(&w->block, w->bytes);
   if (e != cudaSuccess) {
     delete w;
     return cuda_fail(e, "cudaMalloc(solver workspace)");
   }
   char* b = static_cast<char*>(w->block);
-  double** vecs[9] = {&w->x, &w->r, &w->p, &w->q, &w->dinv, &w->res, &w->u, &w->rn, &w->tmp};
-  for (int i = 0; i < 9; ++i) *vecs[i] = reinterpret_cast<double*>(b + i * vb);
-  w->st = reinterpret_cast<PcgState*>(b + 9 * vb);
-  w->dnorm = reinterpret_cast<double*>(b + 9 * vb + 256);
-  e = cudaMallocHost(&w->hst, sizeof(PcgState));
+  double** vecs[10] = {&w->x, &w->r, &w->p, &w->q, &w->dinv, &w->res, &w->u, &w->rn, &w->tmp, &w->p2};
+  for (int i = 0; i < 10; ++i) *vecs[i] = reinterpret_cast<double*>(b + i * vb);
+  w->tile_part = reinterpret_cast<double*>(b + 10 * vb);
+  w->st = reinterpret_cast<PcgState*>(b + 10 * vb + tb);
+  w->dnorm = reinterpret_cast<double*>(b + 10 * vb + tb + 256);
+  w->ticket = reinterpret_cast<unsigned int*>(b + 10 * vb + tb + 512);
+  e = cudaMemset(w->ticket, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMallocHost(&w->hst, sizeof(PcgState));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     cudaFree(w->block);
@@ -99,16 +105,22 @@ static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
   return PFEM_OK;
 }
 
-// One PCG iteration: q = A p, alpha, x/r update (+ flags), new direction.
+// One PCG iteration in two kernels: the fused apply (p = dinv r + beta p_old, q = A p,
+// alpha = rho / p.Ap) and the update (x += alpha p, r -= alpha q, rho, beta, flags).
 static pfem_status pcg_body(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u, cudaStream_t s,
                             cudaGraphConditionalHandle h, int set_cond) {
-  OpArgs a{use_u ? w->u : nullptr, w->p, w->q, nullptr, nullptr, 1.0};
-  pfem_status st = launch_element_op(m->plan, OP_TANGENT, PFEM_F64, ct, a, s);
+  OpArgs a{use_u ? w->u : nullptr, nullptr, w->q, nullptr, nullptr, 1.0};
+  a.pcg.r = w->r;
+  a.pcg.dinv = w->dinv;
+  a.pcg.p[0] = w->p;
+  a.pcg.p[1] = w->p2;
+  a.pcg.st = w->st;
+  a.pcg.tile_part = w->tile_part;
+  a.pcg.ticket = w->ticket;
+  pfem_status st = launch_element_op(m->plan, OP_TANGENT | OP_PCG, PFEM_F64, ct, a, s);
   if (st) return st;
-  if ((st = vk_alpha(w->n, w->p, w->q, w->st, m->red_partials, m->red_counter, s))) return st;
-  if ((st = vk_update(w->n, w->x, w->r, w->p, w->q, w->dinv, w->st, m->red_partials, m->red_counter, h, set_cond, s)))
-    return st;
-  return vk_direction(w->n, w->r, w->dinv, w->p, w->st, s);
+  return vk_update(w->n, w->x, w->r, w->p, w->p2, w->q, w->dinv, w->st, m->red_partials, m->red_counter, h, set_cond,
+                   s);
 }
 
 static pfem_status build_graph(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u, cudaGraphExec_t* out) {
@@ -183,10 +195,11 @@ static pfem_status read_state(pfem_mesh_t m, SolverWS* w) {
 static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u, bool newton_inner) {
   cudaStream_t s = m->stream;
   pfem_status st;
+  // both direction buffers start at zero (the first direction is p = dinv r with beta = 0)
   PFEM_CUDA(cudaMemsetAsync(w->p, 0, (size_t)w->n * sizeof(double), s));
+  PFEM_CUDA(cudaMemsetAsync(w->p2, 0, (size_t)w->n * sizeof(double), s));
   if ((st = true_residual(m, w, newton_inner, s))) return st;
   if ((st = vk_replace(w->n, w->res, w->r, w->dinv, w->st, 1, m->red_partials, m->red_counter, s))) return st;
-  if ((st = vk_direction(w->n, w->r, w->dinv, w->p, w->st, s))) return st;
   cudaGraphExec_t* ex = &w->exec[ct == PFEM_F64][use_u ? 1 : 0];
   const bool use_graph = g_solver_mode == 0 && !w->graph_failed;
   if (use_graph && !*ex) {
@@ -207,7 +220,6 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
     if (w->hst->repl != 0) {
       if ((st = true_residual(m, w, newton_inner, s))) return st;
       if ((st = vk_replace(w->n, w->res, w->r, w->dinv, w->st, 0, m->red_partials, m->red_counter, s))) return st;
-      if ((st = vk_direction(w->n, w->r, w->dinv, w->p, w->st, s))) return st;
       continue;
     }
     if (use_graph && *ex) {

