@@ -360,6 +360,7 @@ def main():
         if not args.quick:
             extras["roofline_large"] = _large_cube(P, pi, torch, peak, peak_kind)
             extras["newton"] = _newton(P, pi, torch)
+            extras["batch_loss"] = _batch_loss(P, pi, torch, np)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -425,6 +426,32 @@ def _large_cube(P, pi, torch, peak, peak_kind):
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": _committed_traffic("cube160_f32v"), "launch_us": us, "algorithmic_bytes": alg,
             "workload": "160^3 x 6 = 24,576,000 tets, 4,173,281 nodes, f32 vectors", "peak_kind": peak_kind}
+
+
+def _batch_loss(P, pi, torch, np):
+    """64-mesh ragged batch (cube / L-shape / holed plate, 5k-200k tets, mixed materials):
+    energy + gradient + Hessian-vector product of every mesh in one element launch."""
+    items = pi.cfg4_batch()
+    meshes = [P.Mesh(p) for p, _ in items]
+    batch = P.Batch(meshes)
+    u = torch.tensor(np.concatenate([uu.reshape(-1) for _, uu in items]), device="cuda")
+    v = torch.randn_like(u)
+    for _ in range(3):
+        batch.eval(u, v, energy=True, grad=True, hvp=True)
+    reps = 20
+    a, b = _events(torch)
+    a.record()
+    for _ in range(reps):
+        batch.eval(u, v, energy=True, grad=True, hvp=True)
+    b.record()
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    n_tets = int(sum(p["conn"].shape[0] for p, _ in items))
+    batch.close()
+    for m in meshes:
+        m.close()
+    return {"meshes": len(items), "tets": n_tets, "ms_per_eval": ms, "evals_per_s": 1e3 / ms,
+            "tets_per_s": n_tets * 1e3 / ms, "ops": "energy + gradient + Hessian-vector, FP32 elements"}
 
 
 def _newton(P, pi, torch):

@@ -60,6 +60,8 @@ typedef enum { PFEM_LINEAR = 0, PFEM_NEOHOOKEAN = 1 } pfem_material_kind;
 typedef enum { PFEM_F32 = 0, PFEM_F64 = 1, PFEM_F64_F32 = 2 } pfem_dtype;
 
 typedef struct pfem_mesh_s* pfem_mesh_t;
+typedef struct pfem_batch_s* pfem_batch_t;
+typedef struct pfem_server_s* pfem_server_t;
 
 /* Problem description (Sec. 2.3.1 point-cloud inputs: geometry, material, boundary
  * conditions). All pointers are HOST pointers, read during pfem_mesh_create only. */
@@ -102,6 +104,8 @@ typedef struct {
   double reference_norm;           /* ref = ||r(u_lift)||: zero free DOFs, prescribed values */
   pfem_status status;
   int64_t kernel_launches;         /* kernels this solve ran (graph replays included) */
+  double queue_s;                  /* serving: submit -> admission (s) */
+  double total_s;                  /* serving: submit -> result ready (s) */
 } pfem_solve_info;
 
 /* ---- mesh ------------------------------------------------------------------------ */
@@ -172,6 +176,65 @@ pfem_status pfem_solve_newton(pfem_mesh_t mesh, pfem_dtype dtype, const double* 
  * as a CUDA graph with a device-side while loop; 1 launches it one iteration at a time with
  * a host-synchronised convergence check (the plain GPU loop used as the serving baseline). */
 pfem_status pfem_set_solver_mode(int32_t mode);
+
+/* ---- ragged batch: energy loss, gradient and Hessian-vector product in one launch --- */
+
+/* The differentiable FE energy loss of Sec. 3.1/3.2 over several meshes at once (the
+ * pretraining loss is summed over a batch of geometries). Groups 3-D meshes (one device;
+ * materials may differ per mesh) for one-launch evaluation. The meshes must outlive the
+ * batch; a batch evaluation uses the meshes' scratch, so it must not overlap on the GPU with
+ * other calls on the same meshes. Batch vectors are the concatenation of the meshes' DOF
+ * vectors in the order given (offsets from pfem_batch_offsets). */
+pfem_status pfem_batch_create(const pfem_mesh_t* meshes, int32_t n_meshes, pfem_batch_t* out);
+void pfem_batch_destroy(pfem_batch_t batch);
+/* offsets[m] = first DOF of mesh m, offsets[n_meshes] = total DOFs (host array). */
+pfem_status pfem_batch_offsets(pfem_batch_t batch, int64_t* offsets);
+
+/* For every mesh m at once (FP32 element arithmetic, FP64 energy sums), with s_m =
+ * mesh_scale[m] (device floats, NULL = 1):
+ *   energy_dev[m] = Pi_m(u)                    if energy_dev != NULL (device doubles)
+ *   grad          = s_m P (f_int(u) - f_ext)   if grad != NULL  (gradient of s_m Pi_m on free DOFs)
+ *   hvp           = s_m P K(u) P v            if hvp != NULL   (Hessian of s_m Pi_m times v; zero
+ *                                                                on prescribed DOFs)
+ * u, v, grad, hvp: float device vectors over the batch's total DOFs. One element launch for
+ * all meshes plus one small energy reduction. Asynchronous on the first mesh's stream.
+ * inverted_dev (device int32, may be NULL) receives the number of elements with J <= 0. */
+pfem_status pfem_batch_eval(pfem_batch_t batch, const float* u, const float* v, const float* mesh_scale,
+                            double* energy_dev, float* grad, float* hvp, int32_t* inverted_dev);
+
+/* ---- serving: continuous batching of warm-started solves -------------------------- */
+
+typedef enum { PFEM_SOLVE_LINEAR = 0, PFEM_SOLVE_NEWTON = 1 } pfem_solve_kind;
+
+/* A server owns planner threads, one worker thread and a CUDA stream on the device current
+ * at creation (Sec. 2.3.2: problems arrive at a platform whose FE iterations refine each
+ * warm start). Requests are planned on the host as they arrive, admitted in arrival order
+ * while a slot is free and their device footprint (mesh plan + solver vectors) fits
+ * hbm_budget_bytes, and then every resident solve advances in shared launches (one fused
+ * element apply over all their tiles and one vector update per PCG step); finished solves
+ * free their slot and memory while the others continue. 3-D meshes only. */
+pfem_status pfem_serve_create(size_t hbm_budget_bytes, int32_t max_slots, pfem_server_t* out);
+
+/* Copies the description and u0 (HOST, n_nodes*dim doubles, NULL = zero start) and queues
+ * the request. kind: pfem_solve_kind (PFEM_SOLVE_LINEAR needs linear material); tol as in
+ * pfem_solve_linear / pfem_solve_newton (inner PCG 1e-8); Newton runs n_load_steps (>= 1).
+ * FP32 element operator, FP64 vectors. *ticket receives the request id. */
+pfem_status pfem_serve_submit(pfem_server_t server, const pfem_mesh_desc* desc, int32_t kind,
+                              const double* u0_host, double tol, int32_t n_load_steps,
+                              uint64_t* ticket);
+
+/* PFEM_PENDING until the request finished; then copies the solution to u_out_host
+ * (n_nodes*dim doubles, may be NULL), fills info (may be NULL, with queue/total latency),
+ * releases the ticket and returns the request's status (OVER_BUDGET if its footprint can
+ * never fit the budget). */
+pfem_status pfem_serve_poll(pfem_server_t server, uint64_t ticket, double* u_out_host,
+                            pfem_solve_info* info);
+
+/* Waits (at most timeout_s) until every submitted request has finished; TIMEOUT otherwise. */
+pfem_status pfem_serve_drain(pfem_server_t server, double timeout_s);
+
+/* Stops the server; requests still running are abandoned. */
+void pfem_serve_destroy(pfem_server_t server);
 
 /* ---- misc ------------------------------------------------------------------------- */
 

@@ -6,7 +6,20 @@ does, and raises if the library has not been built.
 """
 
 from .api import (  # noqa: F401
+    Batch,
     Mesh,
+    Server,
+    pfem_serve_create,
+    pfem_serve_destroy,
+    pfem_serve_drain,
+    pfem_serve_poll,
+    pfem_serve_submit,
+    batch_energy,
+    mesh_energy,
+    pfem_batch_create,
+    pfem_batch_destroy,
+    pfem_batch_eval,
+    pfem_batch_offsets,
     pfem_energy,
     pfem_jacobi_diag,
     pfem_mesh_create,

@@ -72,6 +72,8 @@ class SolveInfo(C.Structure):
         ("reference_norm", C.c_double),
         ("status", C.c_int32),
         ("kernel_launches", C.c_int64),
+        ("queue_s", C.c_double),
+        ("total_s", C.c_double),
     ]
 
 
@@ -91,6 +93,17 @@ SIGNATURES = {
     "pfem_solve_newton": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_int32,
                                       C.c_double, C.c_void_p, C.POINTER(SolveInfo)]),
     "pfem_set_solver_mode": (C.c_int32, [C.c_int32]),
+    "pfem_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "pfem_batch_destroy": (None, [C.c_void_p]),
+    "pfem_batch_offsets": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64)]),
+    "pfem_batch_eval": (C.c_int32, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
+    "pfem_serve_create": (C.c_int32, [C.c_size_t, C.c_int32, C.POINTER(C.c_void_p)]),
+    "pfem_serve_submit": (C.c_int32, [C.c_void_p, C.POINTER(MeshDesc), C.c_int32, C.c_void_p, C.c_double, C.c_int32,
+                                      C.POINTER(C.c_uint64)]),
+    "pfem_serve_poll": (C.c_int32, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(SolveInfo)]),
+    "pfem_serve_drain": (C.c_int32, [C.c_void_p, C.c_double]),
+    "pfem_serve_destroy": (None, [C.c_void_p]),
     "pfem_last_error": (C.c_char_p, []),
     "pfem_version": (C.c_char_p, []),
 }

@@ -98,6 +98,7 @@ class Mesh:
         self.n_nodes = int(desc.n_nodes)
         self.n_elems = int(desc.n_elems)
         self.n_dofs = self.n_nodes * dim
+        self.free_mask = (np.asarray(problem["dirichlet_mask"]).reshape(-1) == 0).astype(np.float64)
         self._arrays = None
 
     def stats(self):
@@ -195,3 +196,228 @@ def pfem_set_solver_mode(mode):
 
 def pfem_version():
     return lib().pfem_version().decode()
+
+
+# ---------------------------------------------------------------------------------------
+# Ragged batches (one element launch for many meshes) and autograd Functions
+# ---------------------------------------------------------------------------------------
+
+
+class Batch:
+    """Owns a pfem_batch_t over 3-D meshes (kept alive by this object)."""
+
+    def __init__(self, meshes):
+        self.meshes = list(meshes)
+        arr = (C.c_void_p * len(self.meshes))(*[m.handle.value for m in self.meshes])
+        h = C.c_void_p()
+        check(lib().pfem_batch_create(arr, len(self.meshes), C.byref(h)))
+        self.handle = h
+        off = (C.c_int64 * (len(self.meshes) + 1))()
+        check(lib().pfem_batch_offsets(self.handle, off))
+        self.offsets = [int(x) for x in off]
+        self.n_meshes = len(self.meshes)
+        self.n_dofs = self.offsets[-1]
+
+    def eval(self, u, v=None, mesh_scale=None, energy=True, grad=False, hvp=False):
+        """Returns (energy float64 (n_meshes,) or None, grad or None, hvp or None)."""
+        n = self.n_dofs
+        up = _dev(u, n, "u")
+        if u.dtype != torch.float32:
+            raise TypeError("batch vectors are float32")
+        e = torch.empty(self.n_meshes, dtype=torch.float64, device=u.device) if energy else None
+        g = torch.empty_like(u) if grad else None
+        h = torch.empty_like(u) if hvp else None
+        vp = _dev(v, n, "v") if v is not None else None
+        sp = _dev(mesh_scale, self.n_meshes, "mesh_scale") if mesh_scale is not None else None
+        check(lib().pfem_batch_eval(self.handle, up, vp, sp, C.c_void_p(e.data_ptr()) if e is not None else None,
+                                    C.c_void_p(g.data_ptr()) if g is not None else None,
+                                    C.c_void_p(h.data_ptr()) if h is not None else None, None))
+        return e, g, h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pfem_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pfem_batch_create(meshes):
+    return Batch(meshes)
+
+
+def pfem_batch_destroy(batch):
+    batch.close()
+
+
+def pfem_batch_offsets(batch):
+    return list(batch.offsets)
+
+
+def pfem_batch_eval(batch, u, v=None, mesh_scale=None, energy=True, grad=False, hvp=False):
+    return batch.eval(u, v, mesh_scale, energy, grad, hvp)
+
+
+class _BatchGrad(torch.autograd.Function):
+    """g = sum_m s_m dPi_m/du (residual kernel); its backward is the Hessian action."""
+
+    @staticmethod
+    def forward(ctx, u, s, batch):
+        ctx.save_for_backward(u, s)
+        ctx.batch = batch
+        return batch.eval(u, mesh_scale=s, energy=False, grad=True)[1]
+
+    @staticmethod
+    def backward(ctx, w):
+        u, s = ctx.saved_tensors
+        hv = ctx.batch.eval(u, v=w.contiguous(), mesh_scale=s, energy=False, hvp=True)[2]
+        return hv, None, None
+
+
+class _BatchEnergy(torch.autograd.Function):
+    """Per-mesh energies Pi_m(u) (FP64 sums of FP32 element terms)."""
+
+    @staticmethod
+    def forward(ctx, u, batch):
+        ctx.save_for_backward(u)
+        ctx.batch = batch
+        return batch.eval(u, energy=True)[0]
+
+    @staticmethod
+    def backward(ctx, ge):
+        (u,) = ctx.saved_tensors
+        s = ge.detach().to(torch.float32).contiguous()
+        return _BatchGrad.apply(u, s, ctx.batch), None
+
+
+def batch_energy(u, batch):
+    """Differentiable per-mesh FE energy loss of a ragged batch (float32 u, float64 output).
+
+    backward = residual kernel (scaled per mesh by the upstream gradient inside the kernel),
+    double backward = tangent kernel (Hessian-vector product); element quantities are
+    recomputed in every pass, never stored.
+    """
+    return _BatchEnergy.apply(u, batch)
+
+
+class _MeshGrad(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, u, mesh):
+        ctx.save_for_backward(u)
+        ctx.mesh = mesh
+        return pfem_residual(ctx.mesh, u)
+
+    @staticmethod
+    def backward(ctx, w):
+        (u,) = ctx.saved_tensors
+        # Hessian of the energy on free DOFs: the kernel reads w as 0 on prescribed DOFs and
+        # returns the identity block there, which the free-DOF mask removes
+        y = pfem_tangent_apply(ctx.mesh, u, w.contiguous())
+        return _zero_prescribed(ctx.mesh, y), None
+
+
+def _zero_prescribed(mesh, y):
+    m = getattr(mesh, "_free_mask", None)
+    if m is None or m.device != y.device or m.dtype != y.dtype:
+        m = torch.as_tensor(mesh.free_mask, dtype=y.dtype, device=y.device)
+        mesh._free_mask = m
+    return y * m
+
+
+class _MeshEnergy(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, u, mesh):
+        ctx.save_for_backward(u)
+        ctx.mesh = mesh
+        e, _ = pfem_energy(mesh, u)
+        return torch.tensor(e, dtype=u.dtype, device=u.device)
+
+    @staticmethod
+    def backward(ctx, ge):
+        (u,) = ctx.saved_tensors
+        return _MeshGrad.apply(u, ctx.mesh) * ge, None
+
+
+def mesh_energy(u, mesh):
+    """Differentiable FE energy of one mesh (float32 or float64 u): backward = residual,
+    double backward = tangent action, prescribed DOFs held fixed (zero gradient)."""
+    return _MeshEnergy.apply(u, mesh)
+
+
+# ---------------------------------------------------------------------------------------
+# Serving
+# ---------------------------------------------------------------------------------------
+
+PFEM_SOLVE_LINEAR, PFEM_SOLVE_NEWTON = 0, 1
+PFEM_PENDING = 8
+
+
+class Server:
+    """pfem_serve_*: continuous batching of warm-started solves on the current device."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=64):
+        h = C.c_void_p()
+        check(lib().pfem_serve_create(C.c_size_t(int(hbm_budget_bytes)), int(max_slots), C.byref(h)))
+        self.handle = h
+        self._dofs = {}
+
+    def submit(self, problem, u0=None, tol=1e-8, solve="linear", n_load_steps=1):
+        """Queue a solve (host arrays); returns its ticket."""
+        desc, arrays = _desc(problem)
+        u0a = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64).reshape(-1)
+        t = C.c_uint64()
+        kind = PFEM_SOLVE_LINEAR if solve == "linear" else PFEM_SOLVE_NEWTON
+        check(lib().pfem_serve_submit(self.handle, C.byref(desc), kind, _ptr(u0a), float(tol), int(n_load_steps),
+                                      C.byref(t)))
+        del arrays
+        self._dofs[t.value] = int(desc.n_nodes) * int(desc.dim)
+        return t.value
+
+    def poll(self, ticket):
+        """None while pending, else (status, u float64 numpy, info dict)."""
+        n = self._dofs[ticket]
+        out = np.empty(n, dtype=np.float64)
+        info = _lib.SolveInfo()
+        st = lib().pfem_serve_poll(self.handle, C.c_uint64(ticket), out.ctypes.data_as(C.c_void_p), C.byref(info))
+        if st == PFEM_PENDING:
+            return None
+        del self._dofs[ticket]
+        return st, out, _info_dict(info)
+
+    def drain(self, timeout_s=600.0):
+        check(lib().pfem_serve_drain(self.handle, float(timeout_s)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pfem_serve_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pfem_serve_create(hbm_budget_bytes, max_slots=64):
+    return Server(hbm_budget_bytes, max_slots)
+
+
+def pfem_serve_submit(server, problem, u0=None, tol=1e-8, solve="linear", n_load_steps=1):
+    return server.submit(problem, u0, tol, solve, n_load_steps)
+
+
+def pfem_serve_poll(server, ticket):
+    return server.poll(ticket)
+
+
+def pfem_serve_drain(server, timeout_s=600.0):
+    server.drain(timeout_s)
+
+
+def pfem_serve_destroy(server):
+    server.close()

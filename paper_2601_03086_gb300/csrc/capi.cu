@@ -60,6 +60,47 @@ pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem
   if (const char* env = std::getenv("PFEM_TILE_ELEMS")) tile_elems = std::atoi(env);
   pfem_status st = build_plan(desc, &hp, &fext, tile_elems);
   if (st != PFEM_OK) return st;
+  return mesh_upload(hp, fext, desc, static_cast<cudaStream_t>(cuda_stream), out);
+}
+
+}  // extern "C"
+
+namespace pfem {
+
+size_t mesh_arena_bytes(const HostPlan& hp) {
+  size_t o = 0;
+  auto take = [&](size_t b) { o = (o + b + 255) & ~size_t(255); };
+  const int64_t nd = hp.n_nodes * hp.dim;
+  take(hp.tile_a.size() * 4);
+  take(hp.tile_b.size() * 4);
+  take(hp.lnode_f.size() * 4);
+  take(hp.lnode_d.size() * 8);
+  take(hp.slot_off.size() * 2 + 2);
+  take(hp.ecode.size() * 2);
+  take(hp.emat_f.size() * 4);
+  take(hp.emat_d.size() * 8);
+  take(hp.halo_info.size() * 4);
+  take(hp.halo_ptr.size() * 4);
+  take(hp.halo_src.size() * 4);
+  take(hp.partial_halo.size() * 4);
+  take((size_t)std::max<int64_t>(hp.n_halo(), 1) * kMaxRegions * sizeof(int32_t));
+  take((size_t)std::max<int64_t>(hp.n_partials, 1) * 4 * sizeof(double) * kMaxRegions);
+  take((size_t)std::max<int64_t>(hp.n_tiles(), 1) * sizeof(double));
+  take(16);
+  take((size_t)nd * 8);
+  take((size_t)nd * 4);
+  take((size_t)nd * 8);
+  take((size_t)nd);
+  take((size_t)kReduceBlocks * 4 * sizeof(double));
+  take(64);
+  take(8 * sizeof(double));
+  return o;
+}
+
+pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, const pfem_mesh_desc* desc,
+                        cudaStream_t stream, pfem_mesh_t* out) {
+  pfem_status st = PFEM_OK;
+  void* cuda_stream = stream;
   const int dim = hp.dim;
   const int64_t nd = hp.n_nodes * dim;
   std::vector<float> fext_f(fext.size());
@@ -196,6 +237,10 @@ pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem
   *out = m;
   return PFEM_OK;
 }
+
+}  // namespace pfem
+
+extern "C" {
 
 pfem_status pfem_plan_check(const pfem_mesh_desc* desc, pfem_mesh_stats* out) {
   HostPlan hp;

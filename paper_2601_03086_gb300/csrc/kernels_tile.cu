@@ -16,7 +16,10 @@
 // Output conventions (Dirichlet DOFs eliminated): tangent y = v on prescribed DOFs and v is
 // read as 0 there; residual r = 0 on prescribed DOFs; diagonal d = 1 on prescribed DOFs.
 
+#include <cuda/atomic>
+
 #include "element.cuh"
+#include "pcg_state.cuh"
 #include "pfem_internal.h"
 
 namespace pfem {
@@ -96,17 +99,19 @@ __device__ __forceinline__ double pcg_direction(const PcgArgs& g, const double* 
 template <int DIM, int OUT, typename VT, typename CT, bool PCG = false>
 __device__ __forceinline__ void final_write(const DevPlan& P, const OpArgs& A, int64_t gid, unsigned mask,
                                             const CT (&acc)[4]) {
+  const CT sc = A.out_scale ? CT(*A.out_scale) : CT(1);  // upstream factor (batched autograd)
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
     const int64_t k = gid * DIM + i;
     const bool fixed = (mask >> i) & 1u;
     if (OUT == OUT_RES) {
       const CT f = fext_ptr<CT>(P)[k];
-      static_cast<VT*>(A.r)[k] = fixed ? VT(0) : VT(acc[i] - CT(A.load_scale) * f);
+      static_cast<VT*>(A.r)[k] = fixed ? VT(0) : VT(sc * (acc[i] - CT(A.load_scale) * f));
     } else if (OUT == OUT_TAN && PCG) {
       static_cast<VT*>(A.y)[k] = fixed ? VT(0) : VT(acc[i]);  // directions vanish on prescribed DOFs
     } else if (OUT == OUT_TAN) {
-      static_cast<VT*>(A.y)[k] = fixed ? static_cast<const VT*>(A.v)[k] : VT(acc[i]);
+      // hess: energy Hessian on free DOFs (zero on prescribed); else the identity block
+      static_cast<VT*>(A.y)[k] = fixed ? (A.hess ? VT(0) : static_cast<const VT*>(A.v)[k]) : VT(sc * acc[i]);
     } else {
       static_cast<VT*>(A.d)[k] = fixed ? VT(1) : VT(acc[i]);
     }
@@ -271,11 +276,11 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
     // halo node: publish this tile's partial, the tile completing the set finishes the node
     const int pi = pbeg + l - ncomp;
     st4(part + 4 * (size_t)pi, acc[0], acc[1], acc[2], CT(0));
-    __threadfence();
     const int h = P.partial_halo[pi];
     const int pb = P.halo_ptr[h], pe = P.halo_ptr[h + 1];
-    if (atomicAdd(count + h, 1) == pe - pb - 1) {
-      __threadfence();
+    // release: this partial is visible before the ticket; acquire: the last tile sees all
+    cuda::atomic_ref<int32_t, cuda::thread_scope_device> ticket(count[h]);
+    if (ticket.fetch_add(1, cuda::memory_order_acq_rel) == pe - pb - 1) {
       CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
       for (int k = pb; k < pe; ++k) {
         CT t[4];
@@ -298,14 +303,15 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
   }
 }
 
+// All passes of tile t of plan P (one CTA). `lay` sizes the shared memory (it may come from
+// a larger plan when several meshes share a launch).
 template <int DIM, int KIND, int OPS, typename VT, typename CT>
-__global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
-  extern __shared__ __align__(32) unsigned char smem[];
+__device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, int t, unsigned char* smem,
+                                             const SmemLayout<CT>& lay) {
   constexpr int NV = DIM + 1;
   constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
-  const SmemLayout<CT> L = smem_layout<CT>(P.max_local, P.slot_cap, NEED_U, NEED_V);
-  const int t = blockIdx.x;
+  const SmemLayout<CT>& L = lay;
   const int4 ta = P.tile_a[t];
   const int4 tb = P.tile_b[t];
   const int ebeg = ta.x, ne = ta.y, lbeg = ta.z, nl = ta.w;
@@ -420,13 +426,13 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
     __shared__ bool s_last;
     if (threadIdx.x == 0) {
       __threadfence();
-      s_last = atomicAdd(A.pcg.ticket, 1u) == gridDim.x - 1;
+      s_last = atomicAdd(A.pcg.ticket, 1u) == (unsigned)P.n_tiles - 1u;
     }
     __syncthreads();
     if (s_last) {
       __threadfence();
       double s = 0.0;
-      for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) s += __ldcg(A.pcg.tile_part + i);
+      for (int i = threadIdx.x; i < P.n_tiles; i += blockDim.x) s += __ldcg(A.pcg.tile_part + i);
       double* red = reinterpret_cast<double*>(smem + L.red);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -451,21 +457,223 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
 }
 
 template <int DIM, int KIND, int OPS, typename VT, typename CT>
+__global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
+  constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
+  const SmemLayout<CT> L = smem_layout<CT>(P.max_local, P.slot_cap, NEED_U, NEED_V);
+  process_tile<DIM, KIND, OPS, VT, CT>(P, A, blockIdx.x, smem, L);
+}
+
+// Ragged batch of 3-D meshes in one launch: CTA b runs tile btile[b].y of mesh btile[b].x
+// (FP32 vectors and arithmetic; linear or Neo-Hookean chosen per mesh, uniform per CTA).
+template <int OPS>
+__global__ void __launch_bounds__(kThreads) batch_kernel(BatchDev B, OpArgs A) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  __shared__ DevPlan sP;
+  const int2 bt = B.btile[blockIdx.x];
+  if (threadIdx.x == 0) sP = B.plans[bt.x];
+  __syncthreads();
+  const int64_t off = B.dof_off[bt.x];
+  OpArgs a = A;
+  a.u = static_cast<const float*>(A.u) + off;
+  if (A.v) a.v = static_cast<const float*>(A.v) + off;
+  if (A.y) a.y = static_cast<float*>(A.y) + off;
+  if (A.r) a.r = static_cast<float*>(A.r) + off;
+  a.out_scale = B.mesh_scale ? B.mesh_scale + bt.x : nullptr;
+  constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
+  const SmemLayout<float> L = smem_layout<float>(B.max_local, B.slot_cap, true, NEED_V);
+  if (sP.kind == PFEM_LINEAR) process_tile<3, K_LIN, OPS, float, float>(sP, a, bt.y, smem, L);
+  else process_tile<3, K_NH, OPS, float, float>(sP, a, bt.y, smem, L);
+}
+
+// Per mesh m (one CTA each): energy[m] = sum of its tile energies - f_ext . u_m.
+__global__ void __launch_bounds__(256) batch_energy_kernel(BatchDev B, const float* u, double* energy) {
+  __shared__ double red[16];
+  const DevPlan& P = B.plans[blockIdx.x];
+  const int64_t off = B.dof_off[blockIdx.x], nd = B.dof_off[blockIdx.x + 1] - off;
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < P.n_tiles; i += blockDim.x) a += P.tile_energy[i];
+  for (int64_t i = threadIdx.x; i < nd; i += blockDim.x) b += P.f_ext[i] * (double)u[off + i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[2 * (threadIdx.x >> 5)] = a;
+    red[2 * (threadIdx.x >> 5) + 1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += red[2 * w];
+      sb += red[2 * w + 1];
+    }
+    energy[blockIdx.x] = sa - sb;
+  }
+}
+
+// Opt a kernel into the largest dynamic shared memory its static shared memory leaves room
+// for (227 KB per CTA in total), once; then check that `need` bytes fit.
+template <typename Kernel>
+static pfem_status allow_dynamic_smem(Kernel kernel, size_t need, int* max_dyn) {
+  if (*max_dyn == 0) {
+    cudaFuncAttributes fa;
+    PFEM_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const int lim = 227 * 1024 - (int)fa.sharedSizeBytes;
+    PFEM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    *max_dyn = lim;
+  }
+  if (need > (size_t)*max_dyn) {
+    set_error("a tile needs %zu bytes of shared memory (at most %d)", need, *max_dyn);
+    return PFEM_ERR_UNSUPPORTED;
+  }
+  return PFEM_OK;
+}
+
+template <int OPS>
+static pfem_status run_batch(const BatchDev& B, const OpArgs& A, int n_blocks, cudaStream_t s) {
+  constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
+  const SmemLayout<float> L = smem_layout<float>(B.max_local, B.slot_cap, true, NEED_V);
+  static int max_dyn = 0;
+  pfem_status st = allow_dynamic_smem(batch_kernel<OPS>, L.total, &max_dyn);
+  if (st) return st;
+  batch_kernel<OPS><<<n_blocks, kThreads, L.total, s>>>(B, A);
+  PFEM_COUNT_LAUNCH();
+  PFEM_CUDA(cudaGetLastError());
+  return PFEM_OK;
+}
+
+pfem_status launch_batch(const BatchDev& B, int n_blocks, int n_meshes, const float* u, const float* v, float* grad,
+                         float* hvp, double* energy, cudaStream_t s) {
+  OpArgs a{};
+  a.u = u;
+  a.v = v;
+  a.y = hvp;
+  a.r = grad;
+  a.load_scale = 1.0;
+  a.hess = 1;  // Hessian of the energy on free DOFs: zero rows and columns on prescribed DOFs
+  pfem_status st;
+  if (grad && hvp) st = run_batch<OP_ENERGY | OP_RESIDUAL | OP_TANGENT>(B, a, n_blocks, s);
+  else if (grad) st = run_batch<OP_ENERGY | OP_RESIDUAL>(B, a, n_blocks, s);
+  else if (hvp) st = run_batch<OP_ENERGY | OP_TANGENT>(B, a, n_blocks, s);
+  else st = run_batch<OP_ENERGY>(B, a, n_blocks, s);
+  if (st) return st;
+  if (energy) {
+    batch_energy_kernel<<<n_meshes, 256, 0, s>>>(B, u, energy);
+    PFEM_COUNT_LAUNCH();
+    PFEM_CUDA(cudaGetLastError());
+  }
+  return PFEM_OK;
+}
+
+// ---- serving: one shared PCG step over all resident solves ------------------------------
+
+__global__ void __launch_bounds__(kThreads) serve_apply_kernel(const ReqDev* reqs, const int2* btile, int max_local,
+                                                               int slot_cap) {
+  extern __shared__ __align__(32) unsigned char smem[];
+  __shared__ ReqDev sR;
+  const int2 bt = btile[blockIdx.x];
+  if (threadIdx.x == 0) sR = reqs[bt.x];
+  __syncthreads();
+  OpArgs a{};
+  a.u = sR.u;
+  a.y = sR.q;
+  a.load_scale = 1.0;
+  a.pcg = sR.pcg;
+  const SmemLayout<float> L = smem_layout<float>(max_local, slot_cap, true, true);
+  constexpr int OPS = OP_TANGENT | OP_PCG;
+  if (sR.plan.kind == PFEM_LINEAR) process_tile<3, K_LIN, OPS, double, float>(sR.plan, a, bt.y, smem, L);
+  else process_tile<3, K_NH, OPS, double, float>(sR.plan, a, bt.y, smem, L);
+}
+
+// x += alpha p; r -= alpha q; r.z and r.r reduced over the solve's own blocks (fixed order),
+// then the shared iteration bookkeeping in the solve's last block.
+__global__ void __launch_bounds__(256) serve_update_kernel(const ReqDev* reqs, const int* ublk) {
+  __shared__ double scratch[16];
+  __shared__ bool s_last;
+  const ReqDev& R = reqs[ublk[blockIdx.x]];
+  PcgState* st = R.pcg.st;
+  if (st->done != 0 || st->repl != 0) return;  // uniform over the solve's blocks
+  const int lb = blockIdx.x - R.ublk0;
+  const double alpha = st->alpha;
+  const double* p = R.pcg.p[(st->iter + 1) & 1];
+  double* x = R.x;
+  double* r = const_cast<double*>(R.pcg.r);
+  const double* q = R.q;
+  const double* dinv = R.pcg.dinv;
+  double v0 = 0.0, v1 = 0.0;
+  for (int64_t i = (int64_t)lb * blockDim.x + threadIdx.x; i < R.n; i += (int64_t)R.nublk * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    v0 += ri * (dinv[i] * ri);
+    v1 += ri * ri;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+    v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    scratch[2 * (threadIdx.x >> 5)] = v0;
+    scratch[2 * (threadIdx.x >> 5) + 1] = v1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a0 = 0.0, a1 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a0 += scratch[2 * w];
+      a1 += scratch[2 * w + 1];
+    }
+    R.upart[2 * lb] = a0;
+    R.upart[2 * lb + 1] = a1;
+    __threadfence();
+    s_last = atomicAdd(R.ucount, 1u) == (unsigned)R.nublk - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    double rz = 0.0, rr = 0.0;
+    for (int b = 0; b < R.nublk; ++b) {
+      rz += __ldcg(R.upart + 2 * b);
+      rr += __ldcg(R.upart + 2 * b + 1);
+    }
+    pcg_finish_update(st, rz, rr);
+    *R.ucount = 0u;
+  }
+}
+
+pfem_status launch_serve_step(const ReqDev* reqs, const int2* btile, int n_apply_blocks, const int* ublk,
+                              int n_update_blocks, int max_local, int slot_cap, cudaStream_t s) {
+  const SmemLayout<float> L = smem_layout<float>(max_local, slot_cap, true, true);
+  static int max_dyn = 0;
+  pfem_status st = allow_dynamic_smem(serve_apply_kernel, L.total, &max_dyn);
+  if (st) return st;
+  if (n_apply_blocks > 0) {
+    serve_apply_kernel<<<n_apply_blocks, kThreads, L.total, s>>>(reqs, btile, max_local, slot_cap);
+    PFEM_COUNT_LAUNCH();
+  }
+  if (n_update_blocks > 0) {
+    serve_update_kernel<<<n_update_blocks, 256, 0, s>>>(reqs, ublk);
+    PFEM_COUNT_LAUNCH();
+  }
+  PFEM_CUDA(cudaGetLastError());
+  return PFEM_OK;
+}
+
+template <int DIM, int KIND, int OPS, typename VT, typename CT>
 static pfem_status run(const DevPlan& P, const OpArgs& A, cudaStream_t s) {
   constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
   const SmemLayout<CT> L = smem_layout<CT>(P.max_local, P.slot_cap, NEED_U, NEED_V);
   if (P.n_tiles <= 0) return PFEM_OK;
-  static int attr_done = 0;  // per instantiation; allow the full 227 KB once
-  if (!attr_done) {
-    PFEM_CUDA(cudaFuncSetAttribute(tile_kernel<DIM, KIND, OPS, VT, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   227 * 1024));
-    attr_done = 1;
-  }
-  if (L.total > 227 * 1024) {
-    set_error("tile needs %zu bytes of shared memory", L.total);
-    return PFEM_ERR_UNSUPPORTED;
-  }
+  static int max_dyn = 0;  // per instantiation
+  pfem_status st = allow_dynamic_smem(tile_kernel<DIM, KIND, OPS, VT, CT>, L.total, &max_dyn);
+  if (st) return st;
   tile_kernel<DIM, KIND, OPS, VT, CT><<<P.n_tiles, kThreads, L.total, s>>>(P, A);
   PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());

@@ -2,6 +2,7 @@
 // dots and norms, deterministic reductions).
 
 #include "kernels_vec.cuh"
+#include "pcg_state.cuh"
 #include "reduce.cuh"
 
 namespace pfem {
@@ -98,21 +99,7 @@ __global__ void __launch_bounds__(kReduceThreads)
     v[1] += ri * ri;
   }
   if (grid_sum<2>(v, partials, counter, scratch) && threadIdx.x == 0) {
-    st->iter += 1;
-    const double rel = sqrt(v[1]) / st->ref;
-    st->rel = rel;
-    if (!isfinite(v[0]) || !isfinite(v[1])) {
-      if (st->done == 0) st->done = PCG_NONFINITE;
-    } else if (st->done == 0) {
-      if (rel < st->tol || rel < st->repl_threshold) {
-        st->repl = 1;  // host verifies / replaces with the FP64 true residual
-      } else if (st->iter >= st->max_iter) {
-        st->done = PCG_MAXITER;
-      } else {
-        st->beta = v[0] / st->rho;
-        st->rho = v[0];
-      }
-    }
+    pcg_finish_update(st, v[0], v[1]);
     if (set_cond) cudaGraphSetConditional(cond, (st->done == 0 && st->repl == 0) ? 1u : 0u);
   }
 }

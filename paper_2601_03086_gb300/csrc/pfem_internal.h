@@ -91,6 +91,11 @@ struct HostPlan {
 // tile_elems <= 0 or > kTileElems selects default_tile_elems(n_elems).
 pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* plan, std::vector<double>* f_ext, int tile_elems = 0);
 
+// Device bytes of a mesh built from hp, and the upload that builds it (capi.cu).
+size_t mesh_arena_bytes(const HostPlan& hp);
+pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, const pfem_mesh_desc* desc,
+                        cudaStream_t stream, pfem_mesh_t* out);
+
 // Default elements per tile for a mesh of n_elems elements.
 int default_tile_elems(int64_t n_elems);
 
@@ -179,7 +184,48 @@ struct OpArgs {
   void* d;          // VT* diagonal output
   double load_scale;
   PcgArgs pcg;      // OP_PCG only
+  const float* out_scale;  // device scalar multiplying residual / tangent outputs (null = 1)
+  int hess;                // tangent on prescribed DOFs: 0 = identity block (y = v), 1 = zero
 };
+
+// A ragged batch of meshes evaluated in one launch (batch.cu builds it).
+struct BatchDev {
+  const DevPlan* plans;    // n_meshes device copies (inverted -> the batch's counter)
+  const int2* btile;       // per launch block: (mesh, tile of that mesh)
+  const int64_t* dof_off;  // n_meshes + 1 DOF offsets into the concatenated vectors
+  const float* mesh_scale; // n_meshes upstream factors for grad / hvp (null = 1)
+  int max_local;           // largest tile node count over the batch
+  int slot_cap;            // largest tile incidence count over the batch
+};
+
+pfem_status launch_batch(const BatchDev& B, int n_blocks, int n_meshes, const float* u, const float* v, float* grad,
+                         float* hvp, double* energy, cudaStream_t s);
+
+// One resident solve of the server (device view). Every active solve takes part in the
+// shared PCG step launches; the reduction of each solve uses its own fixed block count so
+// its rounding does not depend on which other solves share the launch.
+struct ReqDev {
+  DevPlan plan;
+  PcgArgs pcg;             // r, dinv, p[2], st, tile_part, ticket
+  double* q;               // A p
+  double* x;               // iterate (or Newton correction)
+  const double* u;         // Neo-Hookean: linearisation point (null for linear)
+  int64_t n;               // DOFs
+  int ublk0, nublk;        // blocks of the update launch owned by this solve
+  double* upart;           // nublk * 2 partial sums
+  unsigned int* ucount;    // last-block ticket of the update
+};
+
+// Shared PCG step over many solves: fused apply (one CTA per (solve, tile)) then update
+// (one CTA range per solve). btile: (solve, tile) per apply block; ublk: solve per update block.
+pfem_status launch_serve_step(const ReqDev* reqs, const int2* btile, int n_apply_blocks, const int* ublk,
+                              int n_update_blocks, int max_local, int slot_cap, cudaStream_t s);
+
+// Blocks the update launch gives a solve of n DOFs (depends on n only).
+inline int serve_update_blocks(int64_t n) {
+  int64_t b = (n + 256 * 8 - 1) / (256 * 8);
+  return (int)(b < 1 ? 1 : (b > 296 ? 296 : b));
+}
 
 // Launches the tile kernel and the halo pass for one mesh (kernels_tile.cu).
 pfem_status launch_element_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dtype ct,
