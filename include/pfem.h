@@ -147,6 +147,24 @@ pfem_status pfem_residual(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, voi
 pfem_status pfem_tangent_apply(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, const void* v,
                                void* y);
 
+/* Same result as pfem_tangent_apply, for callers that cannot allocate device memory when
+ * they apply the operator (a frozen or exhausted memory pool, code running inside allocator
+ * callbacks, runtimes that only own memory handed to them up front). The paper has no
+ * counterpart: this is a library convenience. The call allocates nothing; the per-call
+ * scratch of the element-tile pass (halo partial sums) lives in a fixed 16 MiB device array
+ * that every GPU loading the library holds until exit. Limits and behaviour:
+ *   - meshes whose halo scratch (n_partials * dim * 4 bytes for F32/F64_F32, * 8 for F64)
+ *     exceeds 16 MiB are rejected with PFEM_ERR_INVALID_ARG;
+ *   - the current device must be the mesh's device (else PFEM_ERR_INVALID_ARG);
+ *   - the first call on a device looks the array's device address up (set-up); make that
+ *     first call before any stream capture;
+ *   - every call shares the one array and it keeps the last call's contents (each call
+ *     overwrites what it reads, so nothing needs clearing); calls that overlap on the GPU,
+ *     on any stream, race on it and must be serialised by the caller.
+ * Arguments, layouts and the other errors are those of pfem_tangent_apply. */
+pfem_status pfem_tangent_apply_noalloc(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, const void* v,
+                                       void* y);
+
 /* d = diag A(u): diag K(u) on free DOFs, 1 on Dirichlet DOFs (the Jacobi preconditioner).
  * u ignored for linear material. Asynchronous. */
 pfem_status pfem_jacobi_diag(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, void* d);
