@@ -37,6 +37,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = ("element-op GB/s vs HBM peak; warm-start solves/s + p50/p99 latency vs plain GPU loop")
+MODES = {"persistent": 0, "plain": 1, "graph": 2}  # pfem_set_solver_mode values
 TOL = 1e-8
 WORKLOAD = {
     "workload": "cube40_lognormal_linear_warm_pcg",
@@ -193,8 +194,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="skip the 160^3 cube, Newton and CPU-oracle extras")
-    ap.add_argument("--solver-mode", default="graph", choices=["graph", "plain"],
-                    help="plain: one launch per kernel (for per-kernel profiler launch lists)")
+    ap.add_argument("--solver-mode", default="persistent", choices=list(MODES),
+                    help="persistent (one cooperative launch per replacement interval), graph (device "
+                         "while loop) or plain (one launch per kernel, for per-kernel profiler launch lists)")
     ap.add_argument("--oracle-worker", nargs=2, type=int, default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.oracle_worker is not None:
@@ -247,8 +249,7 @@ def main():
     def flush_l2():
         flush.fill_(1.0)
 
-    if args.solver_mode == "plain":
-        P.pfem_set_solver_mode(1)
+    P.pfem_set_solver_mode(MODES[args.solver_mode])
     for i in range(args.warmup):
         P.pfem_solve_linear(mesh, warm_d[i], tol=TOL, u_out=u_out)
     torch.cuda.synchronize()
@@ -312,7 +313,18 @@ def main():
             b.record()
             b.synchronize()
             plain_ms.append(a.elapsed_time(b))
-        P.pfem_set_solver_mode(1 if args.solver_mode == "plain" else 0)
+        graph_ms = []
+        P.pfem_set_solver_mode(MODES["graph"])
+        for i in range(min(args.steps, 5)):
+            flush_l2()
+            a, b = _events(torch)
+            a.record()
+            P.pfem_solve_linear(mesh, warm_d[args.warmup + i], tol=TOL, u_out=u_out)
+            b.record()
+            b.synchronize()
+            graph_ms.append(a.elapsed_time(b))
+        extras["graph_loop"] = {"solves_per_s": 1e3 / statistics.mean(graph_ms), "ms_mean": statistics.mean(graph_ms)}
+        P.pfem_set_solver_mode(MODES[args.solver_mode])
         zero_ms, zero_it = [], []
         for i in range(2):
             flush_l2()
@@ -361,6 +373,7 @@ def main():
             extras["roofline_large"] = _large_cube(P, pi, torch, peak, peak_kind)
             extras["newton"] = _newton(P, pi, torch)
             extras["batch_loss"] = _batch_loss(P, pi, torch, np)
+            extras["serving"] = _serving(P, pi, torch, np)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -452,6 +465,92 @@ def _batch_loss(P, pi, torch, np):
         m.close()
     return {"meshes": len(items), "tets": n_tets, "ms_per_eval": ms, "evals_per_s": 1e3 / ms,
             "tets_per_s": n_tets * 1e3 / ms, "ops": "energy + gradient + Hessian-vector, FP32 elements"}
+
+
+def _serving(P, pi, torch, np, n_req=48, rate=1000.0, hi=200_000):
+    """Scaled sample of the serving workload: the first n_req records of the seeded request
+    stream (Poisson arrivals at `rate`/s, 70% linear cubes / 30% Neo-Hookean bars, 50% warm
+    started), mesh sizes log-uniform in [2k, hi] tets (the full stream goes to 2M), tol 1e-8.
+    Served: every request submitted at its arrival time to one server (120 GB admission
+    budget), completions polled; solves/s = requests / makespan, latency = completion -
+    arrival. Plain loop: the same requests one at a time, each creating its mesh and solving
+    with the host-synchronised one-iteration-at-a-time loop. Warm starts are an FP64 solve
+    to 1e-12 on this GPU plus the seeded smooth 1% perturbation (input preparation, untimed)."""
+    reqs = pi.cfg5_requests(n_requests=n_req, seed=5, hi=hi)
+    probs = [pi.request_problem(r) for r in reqs]
+    u0s = []
+    for r, p in zip(reqs, probs):
+        if not r["warm"]:
+            u0s.append(None)
+            continue
+        m = P.Mesh(p)
+        if r["kind"] == "linear":
+            u, _ = P.pfem_solve_linear(m, tol=1e-12, precision="f64")
+        else:
+            u, _ = P.pfem_solve_newton(m, tol=1e-12, n_load_steps=2, precision="f64")
+        u0s.append(pi.make_warm_start(p, u.cpu().numpy(), seed=1 + r["seed"] % 100000))
+        m.close()
+
+    def steps(r, u0):
+        return 1 if (r["kind"] == "linear" or u0 is not None) else 2
+
+    def solve_one(m, r, u0):
+        u0d = None if u0 is None else torch.tensor(u0, device="cuda")
+        if r["kind"] == "linear":
+            u, info = P.pfem_solve_linear(m, u0d, tol=TOL, raise_on_error=False)
+        else:
+            u, info = P.pfem_solve_newton(m, u0d, tol=TOL, n_load_steps=steps(r, u0), raise_on_error=False)
+        return u.cpu(), info
+
+    out = {"requests": n_req, "arrival_rate_per_s": rate, "tets_range": [2000, hi],
+           "tets_total": int(sum(r["n_tets"] for r in reqs)),
+           "linear": sum(r["kind"] == "linear" for r in reqs), "warm": sum(u is not None for u in u0s)}
+    for mode_name, mode in (("plain_loop", MODES["plain"]), ("persistent_loop", MODES["persistent"])):
+        P.pfem_set_solver_mode(mode)
+        torch.cuda.synchronize()
+        lat, ok = [], 0
+        t0 = time.perf_counter()
+        for r, p, u0 in zip(reqs, probs, u0s):
+            a = time.perf_counter()
+            m = P.Mesh(p)
+            _, info = solve_one(m, r, u0)
+            m.close()
+            lat.append(time.perf_counter() - a)
+            ok += info["status"] == 0
+        wall = time.perf_counter() - t0
+        out[mode_name] = {"solves_per_s": n_req / wall, "wall_s": wall, "converged": ok,
+                          "solve_ms_p50": 1e3 * _pct(lat, 0.5), "solve_ms_p99": 1e3 * _pct(lat, 0.99)}
+    P.pfem_set_solver_mode(MODES["persistent"])
+
+    arrive = np.cumsum([r["gap"] for r in reqs]) / rate
+    server = P.Server(120 << 30, max_slots=64)
+    tickets, t_sub, done = [], [], {}
+    t0 = time.perf_counter()
+    i = 0
+    while len(done) < n_req:
+        now = time.perf_counter() - t0
+        while i < n_req and arrive[i] <= now:
+            r = reqs[i]
+            tickets.append(server.submit(probs[i], u0s[i], TOL, r["kind"] if r["kind"] == "linear" else "newton",
+                                         steps(r, u0s[i])))
+            t_sub.append(time.perf_counter() - t0)
+            i += 1
+        for k, t in enumerate(tickets):
+            if k not in done:
+                res = server.poll(t)
+                if res is not None:
+                    done[k] = (time.perf_counter() - t0, res[0], res[2])
+        time.sleep(0.0005)
+    makespan = max(v[0] for v in done.values()) - arrive[0]
+    server.close()
+    lat = [done[k][0] - t_sub[k] for k in range(n_req)]
+    out["served"] = {"solves_per_s": n_req / makespan, "makespan_s": makespan,
+                     "converged": sum(done[k][1] == 0 for k in range(n_req)),
+                     "latency_ms_p50": 1e3 * _pct(lat, 0.5), "latency_ms_p99": 1e3 * _pct(lat, 0.99),
+                     "pcg_iterations_total": int(sum(done[k][2]["iterations"] for k in range(n_req)))}
+    out["speedup_vs_plain_loop"] = out["served"]["solves_per_s"] / out["plain_loop"]["solves_per_s"]
+    out["speedup_vs_persistent_loop"] = out["served"]["solves_per_s"] / out["persistent_loop"]["solves_per_s"]
+    return out
 
 
 def _newton(P, pi, torch):

@@ -1,7 +1,12 @@
 // Per-element arithmetic of the P1 operator (device functions).
 //
 //   geometry (App. A, explicit shape-function differentiation): D = [X_1-X_0 .. X_d-X_0],
-//     dN_a/dX = row a-1 of D^-1 (a >= 1), dN_0/dX = -sum, V = |det D| / d!
+//     dN_a/dX = row a-1 of D^-1 = c_a / det D (a >= 1) with c_a the rows of adj(D) (3-D:
+//     c_1 = d_2 x d_3, c_2 = d_3 x d_1, c_3 = d_1 x d_2), dN_0/dX = -sum, V = |det D| / d!.
+//     The kernels keep c_a unscaled and fold 1/det into one scale per element:
+//     grad w = G'/det with G' = sum_a (w_a - w_0) (x) c_a, and for a stress T,
+//     V T dN_a = T c_a * sgn(det)/d!  (and V (T(G'/det)) dN_a = T(G') c_a / (d! |det|) when T
+//     is linear in the gradient).
 //   linear (Sec. 3.1): eps = sym grad w, sigma = 2 mu eps + lam tr(eps) I, Psi = 1/2 sigma:eps;
 //     force / tangent action  y_a = V sigma(w) dN_a  (f_int = K u for linear FEM, App. B)
 //   Neo-Hookean (Sec. 3.2 energy; App. B total Lagrangian): F = I + grad u, J = det F,
@@ -20,131 +25,150 @@
 namespace pfem {
 
 template <typename T>
-__device__ __forceinline__ T dlog(T x);
+__device__ __forceinline__ T drcp(T x);
 template <>
-__device__ __forceinline__ float dlog<float>(float x) { return logf(x); }
+__device__ __forceinline__ float drcp<float>(float x) { return __frcp_rn(x); }
 template <>
-__device__ __forceinline__ double dlog<double>(double x) { return log(x); }
+__device__ __forceinline__ double drcp<double>(double x) { return 1.0 / x; }
 
-template <int DIM, typename CT>
-struct ElemGeo {
-  CT g[DIM + 1][DIM];
-  CT vol;
+template <int DIM>
+struct Factorial;
+template <>
+struct Factorial<2> {
+  static constexpr double value = 2.0;
+};
+template <>
+struct Factorial<3> {
+  static constexpr double value = 6.0;
 };
 
-// DIM = 3: X[a][i], a = 0..3.
-template <typename CT>
-__device__ __forceinline__ void geometry3(const CT (&X)[4][3], ElemGeo<3, CT>& G) {
-  CT d[3][3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int a = 0; a < 3; ++a) d[i][a] = X[a + 1][i] - X[0][i];
-  const CT c00 = d[1][1] * d[2][2] - d[1][2] * d[2][1];
-  const CT c01 = d[1][2] * d[2][0] - d[1][0] * d[2][2];
-  const CT c02 = d[1][0] * d[2][1] - d[1][1] * d[2][0];
-  const CT det = d[0][0] * c00 + d[0][1] * c01 + d[0][2] * c02;
-  const CT r = CT(1) / det;
-  // inv[a][i] = cofactor(i, a) / det
-  G.g[1][0] = c00 * r;
-  G.g[1][1] = (d[0][2] * d[2][1] - d[0][1] * d[2][2]) * r;
-  G.g[1][2] = (d[0][1] * d[1][2] - d[0][2] * d[1][1]) * r;
-  G.g[2][0] = c01 * r;
-  G.g[2][1] = (d[0][0] * d[2][2] - d[0][2] * d[2][0]) * r;
-  G.g[2][2] = (d[0][2] * d[1][0] - d[0][0] * d[1][2]) * r;
-  G.g[3][0] = c02 * r;
-  G.g[3][1] = (d[0][1] * d[2][0] - d[0][0] * d[2][1]) * r;
-  G.g[3][2] = (d[0][0] * d[1][1] - d[0][1] * d[1][0]) * r;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) G.g[0][i] = -(G.g[1][i] + G.g[2][i] + G.g[3][i]);
-  G.vol = fabs(det) * CT(1.0 / 6.0);
-}
-
-template <typename CT>
-__device__ __forceinline__ void geometry2(const CT (&X)[3][3], ElemGeo<2, CT>& G) {
-  const CT d00 = X[1][0] - X[0][0], d01 = X[2][0] - X[0][0];
-  const CT d10 = X[1][1] - X[0][1], d11 = X[2][1] - X[0][1];
-  const CT det = d00 * d11 - d01 * d10;
-  const CT r = CT(1) / det;
-  G.g[1][0] = d11 * r;
-  G.g[1][1] = -d01 * r;
-  G.g[2][0] = -d10 * r;
-  G.g[2][1] = d00 * r;
-  G.g[0][0] = -(G.g[1][0] + G.g[2][0]);
-  G.g[0][1] = -(G.g[1][1] + G.g[2][1]);
-  G.vol = fabs(det) * CT(0.5);
-}
-
-// grad w: Gw[i][j] = sum_a w_a,i g_a,j
+// c[a][j]: row a of adj(D) (gradient of N_{a+1} times det); det = det D; rdet = 1 / det;
+// s = 1 / (d! |det|) (= V / det^2); kappa = sgn(det) / d! (= V / det).
 template <int DIM, typename CT>
-__device__ __forceinline__ void grad_of(const ElemGeo<DIM, CT>& G, const CT (&w)[DIM + 1][3], CT (&Gw)[DIM][DIM]) {
+struct ElemGeo {
+  CT c[DIM][DIM];
+  CT det, rdet, s, kappa;
+};
+
+// X[a][i], a = 0..DIM (only the first DIM components are used)
+template <int DIM, typename CT>
+__device__ __forceinline__ void geometry(const CT (&X)[DIM + 1][4], ElemGeo<DIM, CT>& G) {
+  if constexpr (DIM == 3) {
+    CT d[3][3];  // d[a][i] = X_{a+1,i} - X_{0,i}
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) d[a][i] = X[a + 1][i] - X[0][i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int b = (a + 1) % 3, e = (a + 2) % 3;  // c_a = d_b x d_e
+      G.c[a][0] = d[b][1] * d[e][2] - d[b][2] * d[e][1];
+      G.c[a][1] = d[b][2] * d[e][0] - d[b][0] * d[e][2];
+      G.c[a][2] = d[b][0] * d[e][1] - d[b][1] * d[e][0];
+    }
+    G.det = d[0][0] * G.c[0][0] + d[0][1] * G.c[0][1] + d[0][2] * G.c[0][2];
+  } else {
+    const CT d00 = X[1][0] - X[0][0], d01 = X[1][1] - X[0][1];  // d_1
+    const CT d10 = X[2][0] - X[0][0], d11 = X[2][1] - X[0][1];  // d_2
+    G.c[0][0] = d11;
+    G.c[0][1] = -d10;
+    G.c[1][0] = -d01;
+    G.c[1][1] = d00;
+    G.det = d00 * d11 - d01 * d10;
+  }
+  G.rdet = drcp<CT>(G.det);
+  const CT inv_fact = CT(1.0 / Factorial<DIM>::value);
+  G.kappa = G.rdet > CT(0) ? inv_fact : -inv_fact;
+  G.s = fabs(G.rdet) * inv_fact;
+}
+
+// Unscaled gradient G' = sum_{a>=1} (w_a - w_0) (x) c_a  (grad w = G' / det)
+template <int DIM, typename CT>
+__device__ __forceinline__ void grad_prime(const ElemGeo<DIM, CT>& G, const CT (&w)[DIM + 1][3], CT (&Gp)[DIM][DIM]) {
+  CT dw[DIM][DIM];
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) dw[a][i] = w[a + 1][i] - w[0][i];
 #pragma unroll
   for (int i = 0; i < DIM; ++i)
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-      // sum_a w_a g_a = sum_{a>=1} (w_a - w_0) g_a since sum_a g_a = 0
-      CT s = (w[1][i] - w[0][i]) * G.g[1][j];
+      CT t = dw[0][i] * G.c[0][j];
 #pragma unroll
-      for (int a = 2; a <= DIM; ++a) s = fma(w[a][i] - w[0][i], G.g[a][j], s);
-      Gw[i][j] = s;
+      for (int a = 1; a < DIM; ++a) t = fma(dw[a][i], G.c[a][j], t);
+      Gp[i][j] = t;
     }
 }
 
-// out_a = V * T g_a (T: DIM x DIM stress-like tensor)
+// grad w = G' / det
 template <int DIM, typename CT>
-__device__ __forceinline__ void contract(const ElemGeo<DIM, CT>& G, const CT (&T)[DIM][DIM], CT (&out)[DIM + 1][DIM]) {
-  CT Tv[DIM][DIM];
+__device__ __forceinline__ void grad_of(const ElemGeo<DIM, CT>& G, const CT (&w)[DIM + 1][3], CT (&Gw)[DIM][DIM]) {
+  grad_prime<DIM, CT>(G, w, Gw);
 #pragma unroll
   for (int i = 0; i < DIM; ++i)
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) Tv[i][j] = T[i][j] * G.vol;
+    for (int j = 0; j < DIM; ++j) Gw[i][j] *= G.rdet;
+}
+
+// out_{a+1} = T c_a, out_0 = -sum (T already carries the element's scale)
+template <int DIM, typename CT>
+__device__ __forceinline__ void contract_c(const ElemGeo<DIM, CT>& G, const CT (&T)[DIM][DIM], CT (&out)[DIM + 1][DIM]) {
 #pragma unroll
-  for (int a = 1; a <= DIM; ++a)
+  for (int a = 0; a < DIM; ++a)
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-      CT s = Tv[i][0] * G.g[a][0];
+      CT t = T[i][0] * G.c[a][0];
 #pragma unroll
-      for (int j = 1; j < DIM; ++j) s = fma(Tv[i][j], G.g[a][j], s);
-      out[a][i] = s;
+      for (int j = 1; j < DIM; ++j) t = fma(T[i][j], G.c[a][j], t);
+      out[a + 1][i] = t;
     }
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
-    CT s = out[1][i];
+    CT t = out[1][i];
 #pragma unroll
-    for (int a = 2; a <= DIM; ++a) s += out[a][i];
-    out[0][i] = -s;
+    for (int a = 2; a <= DIM; ++a) t += out[a][i];
+    out[0][i] = -t;
   }
 }
 
-// linear stress sigma = 2 mu sym(Gw) + lam tr(Gw) I
+// V sigma(G'/det) dN_a for the linear law: sigma(G') scaled by s, contracted with c_a
 template <int DIM, typename CT>
-__device__ __forceinline__ void linear_stress(const CT (&Gw)[DIM][DIM], CT mu, CT lam, CT (&S)[DIM][DIM]) {
-  CT tr = Gw[0][0];
+__device__ __forceinline__ void linear_force(const ElemGeo<DIM, CT>& G, const CT (&Gp)[DIM][DIM], CT mu, CT lam,
+                                             CT (&out)[DIM + 1][DIM]) {
+  const CT mus = mu * G.s, lams = lam * G.s;
+  CT tr = Gp[0][0];
 #pragma unroll
-  for (int i = 1; i < DIM; ++i) tr += Gw[i][i];
+  for (int i = 1; i < DIM; ++i) tr += Gp[i][i];
+  const CT lt = lams * tr;
+  CT S[DIM][DIM];
 #pragma unroll
-  for (int i = 0; i < DIM; ++i)
+  for (int i = 0; i < DIM; ++i) {
+    S[i][i] = fma(CT(2) * mus, Gp[i][i], lt);
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) S[i][j] = mu * (Gw[i][j] + Gw[j][i]);
-#pragma unroll
-  for (int i = 0; i < DIM; ++i) S[i][i] = fma(lam, tr, S[i][i]);
+    for (int j = i + 1; j < DIM; ++j) {
+      S[i][j] = mus * (Gp[i][j] + Gp[j][i]);
+      S[j][i] = S[i][j];
+    }
+  }
+  contract_c<DIM, CT>(G, S, out);
 }
 
+// V Psi for the linear law: s (mu eps':eps' + lam/2 tr'^2), eps' = sym G'
 template <int DIM, typename CT>
-__device__ __forceinline__ CT linear_psi(const CT (&Gw)[DIM][DIM], CT mu, CT lam) {
-  // Psi = mu eps:eps + lam/2 (tr eps)^2
-  CT tr = Gw[0][0];
+__device__ __forceinline__ CT linear_energy(const ElemGeo<DIM, CT>& G, const CT (&Gp)[DIM][DIM], CT mu, CT lam) {
+  CT tr = Gp[0][0];
 #pragma unroll
-  for (int i = 1; i < DIM; ++i) tr += Gw[i][i];
+  for (int i = 1; i < DIM; ++i) tr += Gp[i][i];
   CT ee = CT(0);
 #pragma unroll
   for (int i = 0; i < DIM; ++i)
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-      const CT e = CT(0.5) * (Gw[i][j] + Gw[j][i]);
+      const CT e = CT(0.5) * (Gp[i][j] + Gp[j][i]);
       ee = fma(e, e, ee);
     }
-  return mu * ee + CT(0.5) * lam * tr * tr;
+  return G.s * (mu * ee + CT(0.5) * lam * tr * tr);
 }
 
 // Neo-Hookean kinematics from G = grad u, arranged so that FP32 keeps its relative accuracy
@@ -267,25 +291,37 @@ __device__ __forceinline__ void nh_dpk1(const NHState<DIM, CT>& s, CT mu, CT lam
     }
 }
 
-// Jacobi diagonal entries V [mu |g_a|^2 + (mu + lam - lam lnJ) (H g_a)_i^2]
+// Jacobi diagonal V [mu |g_a|^2 + (mu + lam - lam lnJ) (H g_a)_i^2] = s [mu |c_a|^2 + ... (H c_a)_i^2]
 template <int DIM, typename CT>
-__device__ __forceinline__ void nh_diag(const ElemGeo<DIM, CT>& Ge, const NHState<DIM, CT>* s, CT mu, CT lam,
+__device__ __forceinline__ void nh_diag(const ElemGeo<DIM, CT>& Ge, const NHState<DIM, CT>* st, CT mu, CT lam,
                                         CT (&out)[DIM + 1][DIM]) {
-  const CT lnJ = s ? s->lnJ : CT(0);
+  const CT lnJ = st ? st->lnJ : CT(0);
   const CT c = mu + lam - lam * lnJ;
 #pragma unroll
   for (int a = 0; a <= DIM; ++a) {
+    CT g[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      if (a > 0) {
+        g[j] = Ge.c[a - 1][j];
+      } else {
+        CT t = Ge.c[0][j];
+#pragma unroll
+        for (int b = 1; b < DIM; ++b) t += Ge.c[b][j];
+        g[j] = -t;
+      }
+    }
     CT gg = CT(0);
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) gg = fma(Ge.g[a][j], Ge.g[a][j], gg);
+    for (int j = 0; j < DIM; ++j) gg = fma(g[j], g[j], gg);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) {
-      CT hg = Ge.g[a][i];
-      if (s) {
+      CT hg = g[i];
+      if (st) {
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) hg = fma(s->Hm[i][j], Ge.g[a][j], hg);
+        for (int j = 0; j < DIM; ++j) hg = fma(st->Hm[i][j], g[j], hg);
       }
-      out[a][i] = Ge.vol * fma(c, hg * hg, mu * gg);
+      out[a][i] = Ge.s * fma(c, hg * hg, mu * gg);
     }
   }
 }

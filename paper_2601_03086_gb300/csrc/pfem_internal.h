@@ -141,9 +141,18 @@ enum : int {
   OP_ENERGY = 4,    // per-tile sum of V Psi
   OP_DIAG = 8,      // d = diag A(u)
   OP_PCG = 16,      // with OP_TANGENT: PCG-fused apply (direction update + p.Ap + alpha)
+  OP_PERSIST = 32,  // with OP_PCG: inside the persistent PCG kernel (beta and parity passed in,
+                    // alpha formed by the caller after a grid barrier)
 };
 
-enum : int { PCG_RUNNING = 0, PCG_CONVERGED = 1, PCG_MAXITER = 2, PCG_NONFINITE = 3, PCG_BREAKDOWN = 4 };
+enum : int {
+  PCG_RUNNING = 0,
+  PCG_CONVERGED = 1,
+  PCG_MAXITER = 2,
+  PCG_NONFINITE = 3,
+  PCG_BREAKDOWN = 4,
+  PCG_BARRIER_TIMEOUT = 6,  // a grid barrier of the persistent kernel gave up waiting
+};
 
 // Device-resident scalars of one Jacobi-PCG solve (FP64).
 struct PcgState {
@@ -174,6 +183,33 @@ struct PcgArgs {
   PcgState* st;
   double* tile_part;      // n_tiles doubles
   unsigned int* ticket;   // zero-initialised; reset by the last tile
+  double beta;            // OP_PERSIST: beta of this iteration
+  int odd;                // OP_PERSIST: parity of the completed iteration count
+};
+
+// Grid barrier of the persistent PCG kernel (zeroed before every launch).
+struct GridBar {
+  unsigned int count;  // arrivals at the current barrier
+  unsigned int gen;    // completed barriers
+  int err;             // 1 = some CTA gave up waiting
+  int pad;
+};
+
+// Buffers of the persistent PCG kernel: one launch runs whole iterations (fused direction /
+// apply / p.Ap, grid barrier, alpha and update, grid barrier, beta) until the state asks for
+// an FP64 replacement or terminates.
+struct PersistArgs {
+  const double* u;      // linearisation point of a Newton inner solve (null for linear)
+  double* x;
+  double* r;
+  const double* dinv;
+  double* p[2];
+  double* q;
+  PcgState* st;
+  double* tile_part;    // n_tiles doubles
+  double* red_part;     // kReduceBlocks * 2 doubles
+  GridBar* bar;
+  int64_t n;            // DOFs
 };
 
 struct OpArgs {
@@ -230,6 +266,10 @@ inline int serve_update_blocks(int64_t n) {
 // Launches the tile kernel and the halo pass for one mesh (kernels_tile.cu).
 pfem_status launch_element_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dtype ct,
                               const OpArgs& a, cudaStream_t s);
+
+// Launches the persistent PCG kernel (FP32 element arithmetic only); PFEM_ERR_UNSUPPORTED
+// when it cannot run here (other arithmetic, no co-resident grid), without side effects.
+pfem_status launch_pcg_persistent(const DevPlan& P, pfem_dtype ct, const PersistArgs& a, cudaStream_t s);
 
 // Dynamic shared memory one tile CTA of launch_element_op needs.
 size_t element_op_smem(const DevPlan& P, int ops, pfem_dtype ct);

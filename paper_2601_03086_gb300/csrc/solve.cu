@@ -9,11 +9,14 @@
 // repl_factor since the last replacement, and before declaring convergence: the stopping
 // rule ||f - K u|| / ref < tol is always confirmed with the FP64 operator.
 //
-// The iteration body (apply, alpha, update, direction) is captured once per mesh into a CUDA
-// graph whose while-conditional node repeats it on the device until the state asks for a
-// replacement or terminates, so the host synchronises only a handful of times per solve.
-// The plain mode (pfem_set_solver_mode(1)) launches the same kernels one iteration at a time
-// with a host-synchronised residual check after each iteration.
+// Solver modes (pfem_set_solver_mode), all giving bitwise identical iterates:
+//   0  persistent: one cooperative launch runs iterations until the state asks for a
+//      replacement or terminates (kernels_pcg.cu); FP32 element arithmetic. Where it cannot
+//      run (FP64 arithmetic, no co-resident grid) mode 2 takes over.
+//   1  plain: the two kernels of one iteration at a time, host-synchronised check after each.
+//   2  graph: the iteration body (fused apply + update) captured once per mesh into a CUDA
+//      graph whose while-conditional node repeats it on the device.
+// In modes 0 and 2 the host synchronises only a handful of times per solve.
 
 #include <cmath>
 #include <cstring>
@@ -24,7 +27,7 @@
 
 namespace pfem {
 
-static int g_solver_mode = 0;  // 0 = device while-loop graph, 1 = plain host loop
+static int g_solver_mode = 0;  // 0 = persistent kernel, 1 = plain host loop, 2 = while-loop graph
 
 struct SolverWS {
   int64_t n = 0;
@@ -32,6 +35,8 @@ struct SolverWS {
   double *u = nullptr, *rn = nullptr, *tmp = nullptr, *p2 = nullptr;
   double* tile_part = nullptr;       // per-tile p . A p partials of the fused apply
   unsigned int* ticket = nullptr;    // last-tile ticket of the fused apply
+  GridBar* bar = nullptr;            // grid barrier of the persistent kernel
+  double* red_part = nullptr;        // kReduceBlocks x 2 partials of the persistent kernel
   PcgState* st = nullptr;    // device
   PcgState* hst = nullptr;   // pinned host mirror
   double* dnorm = nullptr;   // device scalar
@@ -41,6 +46,7 @@ struct SolverWS {
   cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [ct][use_u]
   int64_t body_kernels[2][2] = {{0, 0}, {0, 0}};  // kernels per captured iteration
   bool graph_failed = false;
+  bool persist_failed[2] = {false, false};  // [use_u]
 };
 
 __global__ void set_cond_kernel(cudaGraphConditionalHandle h, const PcgState* st) {
@@ -78,7 +84,7 @@ static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
   w->n = m->n_dofs;
   const size_t vb = ((size_t)w->n * sizeof(double) + 255) & ~size_t(255);
   const size_t tb = ((size_t)std::max(m->plan.n_tiles, 1) * sizeof(double) + 255) & ~size_t(255);
-  w->bytes = 10 * vb + tb + 768;
+  w->bytes = 10 * vb + tb + 768 + 4864;
   cudaError_t e = cudaMalloc(&w->block, w->bytes);
   if (e != cudaSuccess) {
     delete w;
@@ -91,6 +97,8 @@ static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
   w->st = reinterpret_cast<PcgState*>(b + 10 * vb + tb);
   w->dnorm = reinterpret_cast<double*>(b + 10 * vb + tb + 256);
   w->ticket = reinterpret_cast<unsigned int*>(b + 10 * vb + tb + 512);
+  w->bar = reinterpret_cast<GridBar*>(b + 10 * vb + tb + 640);
+  w->red_part = reinterpret_cast<double*>(b + 10 * vb + tb + 768);
   e = cudaMemset(w->ticket, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMallocHost(&w->hst, sizeof(PcgState));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking);
@@ -201,7 +209,8 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
   if ((st = true_residual(m, w, newton_inner, s))) return st;
   if ((st = vk_replace(w->n, w->res, w->r, w->dinv, w->st, 1, m->red_partials, m->red_counter, s))) return st;
   cudaGraphExec_t* ex = &w->exec[ct == PFEM_F64][use_u ? 1 : 0];
-  const bool use_graph = g_solver_mode == 0 && !w->graph_failed;
+  bool use_persist = g_solver_mode == 0 && ct != PFEM_F64 && !w->persist_failed[use_u ? 1 : 0];
+  const bool use_graph = (g_solver_mode == 2 || (g_solver_mode == 0 && !use_persist)) && !w->graph_failed;
   if (use_graph && !*ex) {
     if (build_graph(m, w, ct, use_u, ex) != PFEM_OK) {
       w->graph_failed = true;
@@ -222,7 +231,20 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
       if ((st = vk_replace(w->n, w->res, w->r, w->dinv, w->st, 0, m->red_partials, m->red_counter, s))) return st;
       continue;
     }
-    if (use_graph && *ex) {
+    if (use_persist) {
+      PersistArgs pa{use_u ? w->u : nullptr, w->x, w->r, w->dinv, {w->p, w->p2}, w->q, w->st, w->tile_part,
+                     w->red_part, w->bar, w->n};
+      st = launch_pcg_persistent(m->plan, ct, pa, s);
+      if (st == PFEM_OK) continue;
+      if (st != PFEM_ERR_UNSUPPORTED) return st;
+      w->persist_failed[use_u ? 1 : 0] = true;  // falls back to the graph (or plain) loop
+      use_persist = false;
+      if (g_solver_mode == 0 && !w->graph_failed && !*ex && build_graph(m, w, ct, use_u, ex) != PFEM_OK) {
+        w->graph_failed = true;
+        *ex = nullptr;
+      }
+    }
+    if (!w->graph_failed && *ex && g_solver_mode != 1) {
       pending_iter0 = w->hst->iter;
       PFEM_CUDA(cudaGraphLaunch(*ex, s));
     } else {
@@ -272,6 +294,7 @@ static pfem_status status_of(int done) {
     case PCG_CONVERGED: return PFEM_OK;
     case PCG_MAXITER: return PFEM_ERR_NOT_CONVERGED;
     case PCG_NONFINITE: return PFEM_ERR_NONFINITE;
+    case PCG_BARRIER_TIMEOUT: set_error("a grid barrier of the persistent PCG kernel timed out"); return PFEM_ERR_TIMEOUT;
     default: return PFEM_ERR_NOT_CONVERGED;
   }
 }
@@ -283,8 +306,8 @@ using namespace pfem;
 extern "C" {
 
 pfem_status pfem_set_solver_mode(int32_t mode) {
-  if (mode != 0 && mode != 1) {
-    set_error("solver mode must be 0 (graph) or 1 (plain)");
+  if (mode < 0 || mode > 2) {
+    set_error("solver mode must be 0 (persistent), 1 (plain) or 2 (graph)");
     return PFEM_ERR_INVALID_ARG;
   }
   g_solver_mode = mode;

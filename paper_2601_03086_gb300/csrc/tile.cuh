@@ -1,0 +1,474 @@
+// Element-tile kernel: one CTA per tile, shared-memory staging of the tile's nodes, one
+// thread per element (strided), per-incidence slots, fixed-order node sums, and halo nodes
+// finished in-kernel by the last tile to publish its partial.
+//
+// Passes of one tile CTA (every requested output op runs its own element and node pass;
+// element quantities are recomputed, never stored):
+//   stage : tile node coordinates (tile-relative, FP32 or FP64) + u and/or v gathered by id
+//   elem  : per element geometry, kinematics, stress / stress derivative, V * T dN_a into
+//           slot (node, rank); optional V * Psi accumulated per thread
+//   node  : each tile node sums its slots in rank order; a complete node writes its output;
+//           a halo node publishes a partial, and the tile whose partial completes the set
+//           (integer ticket per halo node) sums all partials of that node in ascending tile
+//           order and writes the output. The summation order never depends on timing, so the
+//           result is bitwise reproducible; the ticket is reset by that last tile.
+//
+// Output conventions (Dirichlet DOFs eliminated): tangent y = v on prescribed DOFs and v is
+// read as 0 there; residual r = 0 on prescribed DOFs; diagonal d = 1 on prescribed DOFs.
+
+#pragma once
+
+#include <cuda/atomic>
+
+#include "element.cuh"
+#include "pcg_state.cuh"
+#include "pfem_internal.h"
+
+namespace pfem {
+
+enum : int { K_LIN = 0, K_NH = 1 };
+enum : int { OUT_RES = 0, OUT_TAN = 1, OUT_DIAG = 2 };
+
+template <typename CT>
+struct SmemLayout {
+  size_t slot, x, u, v, off, info, red, total;
+};
+
+// Shared memory: 4-wide (x, y, z, pad) records for slots and staged node data.
+template <typename CT>
+__host__ __device__ inline SmemLayout<CT> smem_layout(int max_local, int slot_cap, bool need_u, bool need_v) {
+  SmemLayout<CT> L;
+  size_t o = 0;
+  auto al = [](size_t x) { return (x + 31) & ~size_t(31); };
+  L.slot = o;
+  o = al(o + (size_t)slot_cap * 4 * sizeof(CT));
+  L.x = o;
+  o = al(o + (size_t)max_local * 4 * sizeof(CT));
+  L.u = o;
+  if (need_u) o = al(o + (size_t)max_local * 4 * sizeof(CT));
+  L.v = o;
+  if (need_v) o = al(o + (size_t)max_local * 4 * sizeof(CT));
+  L.off = o;
+  o = al(o + (size_t)(max_local + 1) * sizeof(int));
+  L.info = o;
+  o = al(o + (size_t)max_local * sizeof(int));
+  L.red = o;
+  o = al(o + 32 * sizeof(double));
+  L.total = o;
+  return L;
+}
+
+// 4-wide loads/stores of compute-type records
+__device__ __forceinline__ void ld4(const float* p, float (&o)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  o[0] = t.x, o[1] = t.y, o[2] = t.z, o[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&o)[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+__device__ __forceinline__ void ldcg4(const float* p, float (&o)[4]) {
+  const float4 t = __ldcg(reinterpret_cast<const float4*>(p));
+  o[0] = t.x, o[1] = t.y, o[2] = t.z, o[3] = t.w;
+}
+__device__ __forceinline__ void ldcg4(const double* p, double (&o)[4]) {
+  const double2 a = __ldcg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldcg(reinterpret_cast<const double2*>(p) + 1);
+  o[0] = a.x, o[1] = a.y, o[2] = b.x, o[3] = b.y;
+}
+
+template <typename CT>
+__device__ __forceinline__ const CT* fext_ptr(const DevPlan& P);
+template <>
+__device__ __forceinline__ const float* fext_ptr<float>(const DevPlan& P) { return P.f_ext_f; }
+template <>
+__device__ __forceinline__ const double* fext_ptr<double>(const DevPlan& P) { return P.f_ext; }
+
+// PCG direction of one DOF: p = dinv r + beta p_old (0 on prescribed DOFs)
+__device__ __forceinline__ double pcg_direction(const PcgArgs& g, const double* p_old, double beta, int64_t k,
+                                                bool fixed) {
+  // r and p_old through L2 only: the persistent kernel rewrites them between grid barriers
+  return fixed ? 0.0 : fma(g.dinv[k], __ldcg(g.r + k), beta * __ldcg(p_old + k));
+}
+
+template <int DIM, int OUT, typename VT, typename CT, bool PCG = false>
+__device__ __forceinline__ void final_write(const DevPlan& P, const OpArgs& A, int64_t gid, unsigned mask,
+                                            const CT (&acc)[4]) {
+  const CT sc = A.out_scale ? CT(*A.out_scale) : CT(1);  // upstream factor (batched autograd)
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    const int64_t k = gid * DIM + i;
+    const bool fixed = (mask >> i) & 1u;
+    if (OUT == OUT_RES) {
+      const CT f = fext_ptr<CT>(P)[k];
+      static_cast<VT*>(A.r)[k] = fixed ? VT(0) : VT(sc * (acc[i] - CT(A.load_scale) * f));
+    } else if (OUT == OUT_TAN && PCG) {
+      static_cast<VT*>(A.y)[k] = fixed ? VT(0) : VT(acc[i]);  // directions vanish on prescribed DOFs
+    } else if (OUT == OUT_TAN) {
+      // hess: energy Hessian on free DOFs (zero on prescribed); else the identity block
+      static_cast<VT*>(A.y)[k] = fixed ? (A.hess ? VT(0) : static_cast<const VT*>(A.v)[k]) : VT(sc * acc[i]);
+    } else {
+      static_cast<VT*>(A.d)[k] = fixed ? VT(1) : VT(acc[i]);
+    }
+  }
+}
+
+// v_e . y_e over the corners of one element (the element's share of v . A v)
+template <int DIM, typename CT>
+__device__ __forceinline__ double corner_dot(const CT (&w)[DIM + 1][3], const CT (&out)[DIM + 1][DIM]) {
+  CT s = CT(0);
+#pragma unroll
+  for (int a = 0; a <= DIM; ++a)
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) s = fma(w[a][i], out[a][i], s);
+  return (double)s;
+}
+
+// One element pass for output OUT (or energy only when OUT < 0). PAP: accumulate v . A_e v
+// into e_acc (tangent pass of the PCG-fused apply).
+template <int DIM, int KIND, int OUT, bool ENERGY, bool COUNT, typename CT, bool PAP = false>
+__device__ __forceinline__ void element_pass(const DevPlan& P, unsigned char* smem, const SmemLayout<CT>& L, int ebeg,
+                                             int ne, double& e_acc, int& n_inv) {
+  constexpr int NV = DIM + 1;
+  const CT* sx = reinterpret_cast<const CT*>(smem + L.x);
+  const CT* su = reinterpret_cast<const CT*>(smem + L.u);
+  const CT* sv = reinterpret_cast<const CT*>(smem + L.v);
+  const int* soff = reinterpret_cast<const int*>(smem + L.off);
+  CT* slot = reinterpret_cast<CT*>(smem + L.slot);
+  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+    const ushort4 code = P.ecode[ebeg + e];
+    const unsigned short cs[4] = {code.x, code.y, code.z, code.w};
+    CT mu, lam;
+    if constexpr (sizeof(CT) == 4) {
+      const float2 m = P.emat_f[ebeg + e];
+      mu = m.x;
+      lam = m.y;
+    } else {
+      const double2 m = P.emat_d[ebeg + e];
+      mu = m.x;
+      lam = m.y;
+    }
+    int loc[NV];
+    CT X[NV][4];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      loc[a] = cs[a] & 1023;
+      ld4(sx + 4 * loc[a], X[a]);
+    }
+    ElemGeo<DIM, CT> G;
+    geometry<DIM, CT>(X, G);
+    constexpr bool NEED_GU = ENERGY || OUT == OUT_RES || (KIND == K_NH && (OUT == OUT_TAN || OUT == OUT_DIAG));
+    auto load_w = [&](const CT* base, CT (&w)[NV][3]) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        CT t[4];
+        ld4(base + 4 * loc[a], t);
+        w[a][0] = t[0], w[a][1] = t[1], w[a][2] = t[2];
+      }
+    };
+    CT out[NV][DIM];
+    if constexpr (KIND == K_LIN) {
+      // linear law: everything from the unscaled gradient G' (grad = G'/det)
+      if constexpr (NEED_GU) {
+        CT w[NV][3], Gp[DIM][DIM];
+        load_w(su, w);
+        grad_prime<DIM, CT>(G, w, Gp);
+        if constexpr (ENERGY) e_acc += (double)linear_energy<DIM, CT>(G, Gp, mu, lam);
+        if constexpr (OUT == OUT_RES) linear_force<DIM, CT>(G, Gp, mu, lam, out);
+      }
+      if constexpr (OUT == OUT_TAN) {
+        CT w[NV][3], Gp[DIM][DIM];
+        load_w(sv, w);
+        grad_prime<DIM, CT>(G, w, Gp);
+        linear_force<DIM, CT>(G, Gp, mu, lam, out);
+        if constexpr (PAP) e_acc += corner_dot<DIM, CT>(w, out);
+      } else if constexpr (OUT == OUT_DIAG) {
+        nh_diag<DIM, CT>(G, static_cast<const NHState<DIM, CT>*>(nullptr), mu, lam, out);
+      }
+    } else {
+      CT Gu[DIM][DIM];
+      {
+        CT w[NV][3];
+        load_w(su, w);
+        grad_of<DIM, CT>(G, w, Gu);
+      }
+      NHState<DIM, CT> s;
+      nh_state<DIM, CT>(Gu, s);
+      if (COUNT && !(s.J > CT(0))) ++n_inv;
+      if constexpr (ENERGY) {
+        const CT psi = s.J > CT(0) ? nh_psi<DIM, CT>(s, mu, lam) : CT(INFINITY);
+        e_acc += (double)(fabs(G.det) * CT(1.0 / Factorial<DIM>::value) * psi);
+      }
+      if constexpr (OUT == OUT_RES || OUT == OUT_TAN) {
+        CT T[DIM][DIM];
+        CT w[NV][3];
+        if constexpr (OUT == OUT_RES) {
+          nh_pk1<DIM, CT>(s, mu, lam, T);
+        } else {
+          CT Gv[DIM][DIM];
+          load_w(sv, w);
+          grad_of<DIM, CT>(G, w, Gv);
+          nh_dpk1<DIM, CT>(s, mu, lam, Gv, T);
+        }
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) T[i][j] *= G.kappa;  // V T dN_a = kappa T c_a
+        contract_c<DIM, CT>(G, T, out);
+        if constexpr (OUT == OUT_TAN && PAP) e_acc += corner_dot<DIM, CT>(w, out);
+      } else if constexpr (OUT == OUT_DIAG) {
+        nh_diag<DIM, CT>(G, &s, mu, lam, out);
+      }
+    }
+    if constexpr (OUT >= 0) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        const int sl = soff[loc[a]] + (cs[a] >> 10);
+        st4(slot + 4 * sl, out[a][0], out[a][1], DIM == 3 ? out[a][DIM - 1] : CT(0), CT(0));
+      }
+    }
+  }
+}
+
+template <int DIM, int OUT, typename VT, typename CT, bool PCG = false>
+__device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, unsigned char* smem,
+                                          const SmemLayout<CT>& L, int nl, int ncomp, int pbeg, int region,
+                                          const double* p_old = nullptr, double* p_new = nullptr, double beta = 0.0) {
+  const int* soff = reinterpret_cast<const int*>(smem + L.off);
+  const int* sinfo = reinterpret_cast<const int*>(smem + L.info);
+  const CT* slot = reinterpret_cast<const CT*>(smem + L.slot);
+  CT* part = static_cast<CT*>(P.partial) + (size_t)region * P.n_partials * 4;
+  int32_t* count = P.halo_count + (size_t)region * P.n_halo;
+  for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    const int b = soff[l], e = soff[l + 1];
+    CT acc[4] = {CT(0), CT(0), CT(0), CT(0)};
+    for (int k = b; k < e; ++k) {
+      CT t[4];
+      ld4(slot + 4 * k, t);
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) acc[i] += t[i];
+    }
+    if (l < ncomp) {
+      const unsigned info = (unsigned)sinfo[l];
+      final_write<DIM, OUT, VT, CT, PCG>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, acc);
+      continue;
+    }
+    // halo node: publish this tile's partial, the tile completing the set finishes the node
+    const int pi = pbeg + l - ncomp;
+    st4(part + 4 * (size_t)pi, acc[0], acc[1], acc[2], CT(0));
+    const int h = P.partial_halo[pi];
+    const int pb = P.halo_ptr[h], pe = P.halo_ptr[h + 1];
+    // release: this partial is visible before the ticket; acquire: the last tile sees all
+    cuda::atomic_ref<int32_t, cuda::thread_scope_device> ticket(count[h]);
+    if (ticket.fetch_add(1, cuda::memory_order_acq_rel) == pe - pb - 1) {
+      CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
+      for (int k = pb; k < pe; ++k) {
+        CT t[4];
+        ldcg4(part + 4 * (size_t)P.halo_src[k], t);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) sum[i] += t[i];
+      }
+      const unsigned hinfo = (unsigned)P.halo_info[h];
+      const int64_t hgid = (int64_t)(hinfo & kInfoIdMask);
+      if constexpr (PCG) {  // the node's new direction, as every tile staged it
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          const int64_t k = hgid * DIM + i;
+          p_new[k] = pcg_direction(A.pcg, p_old, beta, k, ((hinfo >> kInfoIdBits) >> i) & 1u);
+        }
+      }
+      final_write<DIM, OUT, VT, CT, PCG>(P, A, hgid, hinfo >> kInfoIdBits, sum);
+      count[h] = 0;
+    }
+  }
+}
+
+// All passes of tile t of plan P (one CTA). `lay` sizes the shared memory (it may come from
+// a larger plan when several meshes share a launch).
+template <int DIM, int KIND, int OPS, typename VT, typename CT>
+__device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, int t, unsigned char* smem,
+                                             const SmemLayout<CT>& lay) {
+  constexpr int NV = DIM + 1;
+  constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
+  constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
+  const SmemLayout<CT>& L = lay;
+  const int4 ta = P.tile_a[t];
+  const int4 tb = P.tile_b[t];
+  const int ebeg = ta.x, ne = ta.y, lbeg = ta.z, nl = ta.w;
+  const int ncomp = tb.x, pbeg = tb.y;
+  constexpr bool PCG = (OPS & OP_PCG) != 0;
+  const double* p_old = nullptr;
+  double* p_new = nullptr;
+  double beta = 0.0;
+  constexpr bool PERSIST = (OPS & OP_PERSIST) != 0;
+  if constexpr (PCG) {
+    bool odd;
+    if constexpr (PERSIST) {  // the persistent kernel passes the state of this iteration
+      beta = A.pcg.beta;
+      odd = A.pcg.odd != 0;
+    } else {
+      // the state is written only by earlier kernels, so every CTA takes the same branch
+      const PcgState* st = A.pcg.st;
+      if (st->done != 0 || st->repl != 0) return;
+      beta = st->beta;
+      odd = (st->iter & 1) != 0;
+    }
+    // select, not index: keeps the arguments out of local memory
+    p_old = odd ? A.pcg.p[1] : A.pcg.p[0];
+    p_new = odd ? A.pcg.p[0] : A.pcg.p[1];
+  }
+
+  // ---- stage tile nodes
+  {
+    CT* sx = reinterpret_cast<CT*>(smem + L.x);
+    CT* su = reinterpret_cast<CT*>(smem + L.u);
+    CT* sv = reinterpret_cast<CT*>(smem + L.v);
+    int* soff = reinterpret_cast<int*>(smem + L.off);
+    int* sinfo = reinterpret_cast<int*>(smem + L.info);
+    const VT* u = static_cast<const VT*>(A.u);
+    const VT* v = static_cast<const VT*>(A.v);
+    for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+      const float4 rf = P.lnode_f[lbeg + l];
+      const int info = __float_as_int(rf.w);
+      if constexpr (sizeof(CT) == 4) {
+        st4(sx + 4 * l, rf.x, rf.y, rf.z, 0.f);
+      } else {
+        const PfemDouble4 rd = P.lnode_d[lbeg + l];
+        st4(sx + 4 * l, rd.x, rd.y, rd.z, 0.0);
+      }
+      sinfo[l] = info;
+      soff[l] = (int)P.slot_off[lbeg + l];
+      const int64_t gid = (int64_t)((unsigned)info & kInfoIdMask);
+      const unsigned mask = (unsigned)info >> kInfoIdBits;
+      if constexpr (NEED_U) {
+        CT w[3] = {CT(0), CT(0), CT(0)};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) w[i] = CT(u[gid * DIM + i]);
+        st4(su + 4 * l, w[0], w[1], w[2], CT(0));
+      }
+      if constexpr (PCG) {
+        CT w[3] = {CT(0), CT(0), CT(0)};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+          const int64_t k = gid * DIM + i;
+          const double pn = pcg_direction(A.pcg, p_old, beta, k, (mask >> i) & 1u);
+          if (l < ncomp) p_new[k] = pn;  // complete nodes: this tile owns the DOF
+          w[i] = CT(pn);
+        }
+        st4(sv + 4 * l, w[0], w[1], w[2], CT(0));
+      } else if constexpr (NEED_V) {
+        CT w[3] = {CT(0), CT(0), CT(0)};
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) w[i] = ((mask >> i) & 1u) ? CT(0) : CT(v[gid * DIM + i]);
+        st4(sv + 4 * l, w[0], w[1], w[2], CT(0));
+      }
+    }
+    if (threadIdx.x == 0) soff[nl] = ne * NV;
+  }
+  __syncthreads();
+
+  double e_acc = 0.0;
+  int n_inv = 0;
+  int region = 0;
+  if constexpr ((OPS & OP_RESIDUAL) != 0) {
+    element_pass<DIM, KIND, OUT_RES, (OPS & OP_ENERGY) != 0, true, CT>(P, smem, L, ebeg, ne, e_acc, n_inv);
+    __syncthreads();
+    node_pass<DIM, OUT_RES, VT, CT>(P, A, smem, L, nl, ncomp, pbeg, region++);
+    __syncthreads();
+  } else if constexpr ((OPS & OP_ENERGY) != 0) {
+    element_pass<DIM, KIND, -1, true, true, CT>(P, smem, L, ebeg, ne, e_acc, n_inv);
+  }
+  if constexpr ((OPS & OP_TANGENT) != 0) {
+    element_pass<DIM, KIND, OUT_TAN, false, (OPS & (OP_RESIDUAL | OP_ENERGY)) == 0, CT, PCG>(P, smem, L, ebeg, ne,
+                                                                                          e_acc, n_inv);
+    __syncthreads();
+    node_pass<DIM, OUT_TAN, VT, CT, PCG>(P, A, smem, L, nl, ncomp, pbeg, region++, p_old, p_new, beta);
+    __syncthreads();
+  }
+  if constexpr ((OPS & OP_DIAG) != 0) {
+    element_pass<DIM, KIND, OUT_DIAG, false, (OPS & (OP_RESIDUAL | OP_ENERGY | OP_TANGENT)) == 0, CT>(
+        P, smem, L, ebeg, ne, e_acc, n_inv);
+    __syncthreads();
+    node_pass<DIM, OUT_DIAG, VT, CT>(P, A, smem, L, nl, ncomp, pbeg, region++);
+  }
+  if constexpr (KIND == K_NH) {
+    const int tot = __reduce_add_sync(0xffffffffu, n_inv);
+    if ((threadIdx.x & 31) == 0 && tot > 0 && P.inverted) atomicAdd(P.inverted, tot);
+  }
+  if constexpr ((OPS & OP_ENERGY) != 0 || PCG) {
+    // tile sum of the energy (or of p_e . A_e p_e): warp butterflies, warps in index order
+    double* red = reinterpret_cast<double*>(smem + L.red);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e_acc += __shfl_xor_sync(0xffffffffu, e_acc, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e_acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+      if constexpr (PCG) A.pcg.tile_part[t] = s;
+      else P.tile_energy[t] = s;
+    }
+  }
+  if constexpr (PCG && !PERSIST) {
+    // the last tile to finish sums the tile partials in tile order: alpha = rho / (p . A p)
+    __shared__ bool s_last;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      s_last = atomicAdd(A.pcg.ticket, 1u) == (unsigned)P.n_tiles - 1u;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      double s = 0.0;
+      for (int i = threadIdx.x; i < P.n_tiles; i += blockDim.x) s += __ldcg(A.pcg.tile_part + i);
+      double* red = reinterpret_cast<double*>(smem + L.red);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      __syncthreads();
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double pap = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pap += red[w];
+        PcgState* st = A.pcg.st;
+        // negative curvature does not stop plain CG; p.Ap = 0 or non-finite does
+        if (pap == 0.0 || !isfinite(pap)) {
+          st->alpha = 0.0;
+          st->done = isfinite(pap) ? PCG_BREAKDOWN : PCG_NONFINITE;
+        } else {
+          st->alpha = st->rho / pap;
+        }
+        *A.pcg.ticket = 0u;
+      }
+    }
+  }
+}
+
+// Opt a kernel into the largest dynamic shared memory its static shared memory leaves room
+// for (227 KB per CTA in total), once; then check that `need` bytes fit.
+template <typename Kernel>
+static inline pfem_status allow_dynamic_smem(Kernel kernel, size_t need, int* max_dyn) {
+  if (*max_dyn == 0) {
+    cudaFuncAttributes fa;
+    PFEM_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const int lim = 227 * 1024 - (int)fa.sharedSizeBytes;
+    PFEM_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim));
+    *max_dyn = lim;
+  }
+  if (need > (size_t)*max_dyn) {
+    set_error("a tile needs %zu bytes of shared memory (at most %d)", need, *max_dyn);
+    return PFEM_ERR_UNSUPPORTED;
+  }
+  return PFEM_OK;
+}
+
+}  // namespace pfem

@@ -3,9 +3,10 @@
     python -m paper_2601_03086_gb300.probe apply --n 160 --reps 3 [--vec f64] [--kind nh]
         tangent apply on the n^3 x 6 Kuhn cube (FP32 element arithmetic; f64 = FP64
         vectors with FP32 arithmetic, the PCG configuration)
-    python -m paper_2601_03086_gb300.probe solve --n 40 --max-iter 40 [--plain]
-        Jacobi-PCG on the n^3 cube (the benchmark workload at n = 40); --plain launches one
-        kernel at a time so a profiler can attribute time per kernel
+    python -m paper_2601_03086_gb300.probe solve --n 40 --max-iter 40 [--mode plain]
+        Jacobi-PCG on the n^3 cube (the benchmark workload at n = 40); --mode persistent
+        (default), graph, or plain (one kernel at a time, so a profiler can attribute time
+        per kernel); --reps solves after one warm-up solve
 Prints one JSON line with the timings (CUDA events, after warm-up).
 """
 
@@ -27,7 +28,7 @@ def main(argv=None):
     ap.add_argument("--vec", choices=["f32", "f64"], default="f32")
     ap.add_argument("--kind", choices=["linear", "nh"], default="linear")
     ap.add_argument("--max-iter", type=int, default=100000)
-    ap.add_argument("--plain", action="store_true")
+    ap.add_argument("--mode", choices=["persistent", "plain", "graph"], default="persistent")
     a = ap.parse_args(argv)
 
     import torch
@@ -58,14 +59,17 @@ def main(argv=None):
         ev[1].synchronize()
         out["apply_us"] = ev[0].elapsed_time(ev[1]) * 1e3 / a.reps
     else:
-        if a.plain:
-            P.pfem_set_solver_mode(1)
+        P.pfem_set_solver_mode({"persistent": 0, "plain": 1, "graph": 2}[a.mode])
+        P.pfem_solve_linear(mesh, tol=1e-8, max_iter=a.max_iter, raise_on_error=False)
         ev[0].record()
-        _, info = P.pfem_solve_linear(mesh, tol=1e-8, max_iter=a.max_iter, raise_on_error=False)
+        for _ in range(a.reps):
+            _, info = P.pfem_solve_linear(mesh, tol=1e-8, max_iter=a.max_iter, raise_on_error=False)
         ev[1].record()
         ev[1].synchronize()
-        out["solve_ms"] = ev[0].elapsed_time(ev[1])
+        out["solve_ms"] = ev[0].elapsed_time(ev[1]) / a.reps
         out["iterations"] = info["iterations"]
+        out["us_per_iteration"] = 1e3 * out["solve_ms"] / max(info["iterations"], 1)
+        out["mode"] = a.mode
     print(json.dumps(out))
     mesh.close()
     return 0

@@ -67,13 +67,39 @@ def test_solver_modes_bitwise_equal_and_deterministic():
     p = pi.cube_problem(8, seed=3)
     mesh = P.Mesh(p)
     outs = []
-    for mode in (0, 0, 1):
+    for mode in (0, 0, 1, 2):  # persistent twice, plain, graph
         P.pfem_set_solver_mode(mode)
         u, info = P.pfem_solve_linear(mesh, tol=1e-8)
         outs.append((host(u), info["iterations"]))
     P.pfem_set_solver_mode(0)
-    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][0], outs[2][0])
-    assert outs[0][1] == outs[1][1] == outs[2][1]
+    for o in outs[1:]:
+        assert np.array_equal(outs[0][0], o[0])
+        assert outs[0][1] == o[1]
+
+
+def test_solver_modes_bitwise_equal_newton_and_2d():
+    P = pfem()
+    cases = [(pi.bar_problem(8, 2, 2, seed=5), "newton"), (pi.cfg1_plate(), "linear")]
+    for p, kind in cases:
+        mesh = P.Mesh(p)
+        outs = []
+        for mode in (0, 1, 2):
+            P.pfem_set_solver_mode(mode)
+            if kind == "newton":
+                u, info = P.pfem_solve_newton(mesh, tol=1e-8, n_load_steps=2)
+            else:
+                u, info = P.pfem_solve_linear(mesh, tol=1e-8)
+            outs.append((host(u), info["iterations"]))
+        P.pfem_set_solver_mode(0)
+        for o in outs[1:]:
+            assert np.array_equal(outs[0][0], o[0]), kind
+            assert outs[0][1] == o[1], kind
+
+
+def test_solver_mode_rejects_unknown():
+    P = pfem()
+    with pytest.raises(RuntimeError):
+        P.pfem_set_solver_mode(3)
 
 
 def test_skip_test_returns_without_iterating():
