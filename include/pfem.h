@@ -91,6 +91,9 @@ typedef struct {
   int64_t n_partials;       /* (tile, halo node) pairs */
   int64_t device_bytes;     /* device memory held by the mesh */
   int32_t max_tile_elems, max_tile_nodes;
+  int64_t n_fans;           /* element fans (chains of simplices around a hinge, one per thread) */
+  int32_t max_tile_slots;   /* largest per-tile count of (fan, node) contribution slots */
+  int32_t reserved;
 } pfem_mesh_stats;
 
 typedef struct {

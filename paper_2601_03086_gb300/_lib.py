@@ -57,6 +57,9 @@ class MeshStats(C.Structure):
         ("device_bytes", C.c_int64),
         ("max_tile_elems", C.c_int32),
         ("max_tile_nodes", C.c_int32),
+        ("n_fans", C.c_int64),
+        ("max_tile_slots", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 

@@ -52,13 +52,14 @@ pfem_status pfem_batch_create(const pfem_mesh_t* meshes, int32_t n, pfem_batch_t
   b->device = meshes[0]->device;
   b->off.assign((size_t)n + 1, 0);
   std::vector<int2> btile;
-  int max_local = 0, slot_cap = 0;
+  int max_local = 0, slot_cap = 0, step_cap = 0;
   for (int i = 0; i < n; ++i) {
     const DevPlan& P = meshes[i]->plan;
     b->off[(size_t)i + 1] = b->off[(size_t)i] + meshes[i]->n_dofs;
     for (int t = 0; t < P.n_tiles; ++t) btile.push_back(make_int2(i, t));
     max_local = std::max(max_local, P.max_local);
     slot_cap = std::max(slot_cap, P.slot_cap);
+    step_cap = std::max(step_cap, P.step_cap);
   }
   b->n_blocks = (int)btile.size();
   const size_t o_plans = 0;
@@ -95,6 +96,7 @@ pfem_status pfem_batch_create(const pfem_mesh_t* meshes, int32_t n, pfem_batch_t
   b->dev.mesh_scale = nullptr;
   b->dev.max_local = max_local;
   b->dev.slot_cap = slot_cap;
+  b->dev.step_cap = step_cap;
   *out = b;
   return PFEM_OK;
 }

@@ -76,9 +76,11 @@ size_t mesh_arena_bytes(const HostPlan& hp) {
   take(hp.lnode_f.size() * 4);
   take(hp.lnode_d.size() * 8);
   take(hp.slot_off.size() * 2 + 2);
-  take(hp.ecode.size() * 2);
-  take(hp.emat_f.size() * 4);
-  take(hp.emat_d.size() * 8);
+  take(hp.tile_cnt.size() * 2);
+  take(hp.fan_head.size() * 2);
+  take(hp.step_code.size() * 2);
+  take(hp.step_mat_f.size() * 4);
+  take(hp.step_mat_d.size() * 8);
   take(hp.halo_info.size() * 4);
   take(hp.halo_ptr.size() * 4);
   take(hp.halo_src.size() * 4);
@@ -123,9 +125,11 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   const size_t o_lf = ab.take(hp.lnode_f.size() * 4);
   const size_t o_ld = ab.take(hp.lnode_d.size() * 8);
   const size_t o_so = ab.take(hp.slot_off.size() * 2 + 2);
-  const size_t o_ec = ab.take(hp.ecode.size() * 2);
-  const size_t o_mf = ab.take(hp.emat_f.size() * 4);
-  const size_t o_md = ab.take(hp.emat_d.size() * 8);
+  const size_t o_tc = ab.take(hp.tile_cnt.size() * 2);
+  const size_t o_fh = ab.take(hp.fan_head.size() * 2);
+  const size_t o_sc = ab.take(hp.step_code.size() * 2);
+  const size_t o_mf = ab.take(hp.step_mat_f.size() * 4);
+  const size_t o_md = ab.take(hp.step_mat_d.size() * 8);
   const size_t o_hi = ab.take(hp.halo_info.size() * 4);
   const size_t o_hp = ab.take(hp.halo_ptr.size() * 4);
   const size_t o_hs = ab.take(hp.halo_src.size() * 4);
@@ -173,8 +177,9 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   };
   if ((st = upload(base, o_ta, hp.tile_a, s)) || (st = upload(base, o_tb, hp.tile_b, s)) ||
       (st = upload(base, o_lf, hp.lnode_f, s)) || (st = upload(base, o_ld, hp.lnode_d, s)) ||
-      (st = upload(base, o_so, hp.slot_off, s)) || (st = upload(base, o_ec, hp.ecode, s)) ||
-      (st = upload(base, o_mf, hp.emat_f, s)) || (st = upload(base, o_md, hp.emat_d, s)) ||
+      (st = upload(base, o_so, hp.slot_off, s)) || (st = upload(base, o_tc, hp.tile_cnt, s)) ||
+      (st = upload(base, o_fh, hp.fan_head, s)) || (st = upload(base, o_sc, hp.step_code, s)) ||
+      (st = upload(base, o_mf, hp.step_mat_f, s)) || (st = upload(base, o_md, hp.step_mat_d, s)) ||
       (st = upload(base, o_hi, hp.halo_info, s)) || (st = upload(base, o_hp, hp.halo_ptr, s)) ||
       (st = upload(base, o_hs, hp.halo_src, s)) || (st = upload(base, o_ph, hp.partial_halo, s)) ||
       (st = upload(base, o_fe, fext, s)) ||
@@ -193,7 +198,8 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   P.n_tiles = (int)nt;
   P.n_halo = (int)hp.n_halo();
   P.max_local = hp.max_local;
-  P.slot_cap = hp.max_elems * hp.nv;
+  P.slot_cap = std::max(hp.max_slots, 1);
+  P.step_cap = std::max(hp.max_elems, 1);
   P.n_nodes = hp.n_nodes;
   P.n_partials = hp.n_partials;
   P.tile_a = reinterpret_cast<const int4*>(base + o_ta);
@@ -201,9 +207,11 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   P.lnode_f = reinterpret_cast<const float4*>(base + o_lf);
   P.lnode_d = reinterpret_cast<const PfemDouble4*>(base + o_ld);
   P.slot_off = reinterpret_cast<const uint16_t*>(base + o_so);
-  P.ecode = reinterpret_cast<const ushort4*>(base + o_ec);
-  P.emat_f = reinterpret_cast<const float2*>(base + o_mf);
-  P.emat_d = reinterpret_cast<const double2*>(base + o_md);
+  P.tile_cnt = reinterpret_cast<const uint4*>(base + o_tc);
+  P.fan_head = reinterpret_cast<const ushort4*>(base + o_fh);
+  P.step_code = reinterpret_cast<const uint16_t*>(base + o_sc);
+  P.step_mat_f = reinterpret_cast<const float2*>(base + o_mf);
+  P.step_mat_d = reinterpret_cast<const double2*>(base + o_md);
   P.halo_info = reinterpret_cast<const int32_t*>(base + o_hi);
   P.halo_ptr = reinterpret_cast<const int32_t*>(base + o_hp);
   P.halo_src = reinterpret_cast<const int32_t*>(base + o_hs);
@@ -234,6 +242,8 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   S.device_bytes = (int64_t)ab.off;
   S.max_tile_elems = hp.max_elems;
   S.max_tile_nodes = hp.max_local;
+  S.n_fans = hp.n_fans;
+  S.max_tile_slots = hp.max_slots;
   *out = m;
   return PFEM_OK;
 }
@@ -245,7 +255,9 @@ extern "C" {
 pfem_status pfem_plan_check(const pfem_mesh_desc* desc, pfem_mesh_stats* out) {
   HostPlan hp;
   std::vector<double> fext;
-  pfem_status st = build_plan(desc, &hp, &fext);
+  int tile_elems = 0;
+  if (const char* env = std::getenv("PFEM_TILE_ELEMS")) tile_elems = std::atoi(env);
+  pfem_status st = build_plan(desc, &hp, &fext, tile_elems);
   if (st != PFEM_OK) return st;
   if ((st = verify_plan(desc, hp)) != PFEM_OK) return st;
   if (out) {
@@ -263,6 +275,8 @@ pfem_status pfem_plan_check(const pfem_mesh_desc* desc, pfem_mesh_stats* out) {
     out->n_partials = hp.n_partials;
     out->max_tile_elems = hp.max_elems;
     out->max_tile_nodes = hp.max_local;
+    out->n_fans = hp.n_fans;
+    out->max_tile_slots = hp.max_slots;
   }
   return PFEM_OK;
 }

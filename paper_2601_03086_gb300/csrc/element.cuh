@@ -82,6 +82,51 @@ __device__ __forceinline__ void geometry(const CT (&X)[DIM + 1][4], ElemGeo<DIM,
   G.s = fabs(G.rdet) * inv_fact;
 }
 
+// Simplex i of a fan: corners (h_0, h_1, r_i, r_{i+1}) in 3-D, (h_0, r_i, r_{i+1}) in 2-D,
+// from the edges Ei = r_i - h_0, En = r_{i+1} - h_0 and (3-D) H = h_1 - h_0 with
+// Qj = H x Ej, each formed once per ring node: the adjugate rows are
+//   3-D: c_1 = Ei x En, c_2 = En x H = -Qn, c_3 = H x Ei = Qi, det = H . c_1
+//   2-D: c_1 = (En_y, -En_x), c_2 = (-Ei_y, Ei_x), det = Ei_x En_y - Ei_y En_x
+template <int DIM, typename CT>
+__device__ __forceinline__ void fan_geometry(const CT (&H)[3], const CT (&Ei)[3], const CT (&En)[3], const CT (&Qi)[3],
+                                             const CT (&Qn)[3], ElemGeo<DIM, CT>& G) {
+  if constexpr (DIM == 3) {
+    G.c[0][0] = Ei[1] * En[2] - Ei[2] * En[1];
+    G.c[0][1] = Ei[2] * En[0] - Ei[0] * En[2];
+    G.c[0][2] = Ei[0] * En[1] - Ei[1] * En[0];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      G.c[1][j] = -Qn[j];
+      G.c[2][j] = Qi[j];
+    }
+    G.det = H[0] * G.c[0][0] + H[1] * G.c[0][1] + H[2] * G.c[0][2];
+  } else {
+    G.c[0][0] = En[1];
+    G.c[0][1] = -En[0];
+    G.c[1][0] = -Ei[1];
+    G.c[1][1] = Ei[0];
+    G.det = Ei[0] * En[1] - Ei[1] * En[0];
+  }
+  G.rdet = drcp<CT>(G.det);
+  const CT inv_fact = CT(1.0 / Factorial<DIM>::value);
+  G.kappa = G.rdet > CT(0) ? inv_fact : -inv_fact;
+  G.s = fabs(G.rdet) * inv_fact;
+}
+
+// G' from corner differences dw[a] = w_{a+1} - w_0 (a < DIM)
+template <int DIM, typename CT>
+__device__ __forceinline__ void grad_prime_d(const ElemGeo<DIM, CT>& G, const CT (&dw)[DIM][3], CT (&Gp)[DIM][DIM]) {
+#pragma unroll
+  for (int i = 0; i < DIM; ++i)
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      CT t = dw[0][i] * G.c[0][j];
+#pragma unroll
+      for (int a = 1; a < DIM; ++a) t = fma(dw[a][i], G.c[a][j], t);
+      Gp[i][j] = t;
+    }
+}
+
 // Unscaled gradient G' = sum_{a>=1} (w_a - w_0) (x) c_a  (grad w = G' / det)
 template <int DIM, typename CT>
 __device__ __forceinline__ void grad_prime(const ElemGeo<DIM, CT>& G, const CT (&w)[DIM + 1][3], CT (&Gp)[DIM][DIM]) {

@@ -1,20 +1,20 @@
 // Persistent Jacobi-PCG kernel (App. B linear system, Sec. 2.3.2 warm start): one cooperative
-// launch keeps every CTA resident and runs whole iterations of the two-kernel body
+// launch keeps every CTA resident and runs whole iterations of the two-kernel body of the
+// graph mode, with grid barriers where the graph has kernel boundaries:
 //
-//   A  tiles (round robin over CTAs): p = dinv r + beta p_old on the fly, q = A p,
-//      per-tile p_e . A_e p_e                                    -> grid barrier
-//   B  alpha = rho / sum(tile sums); x += alpha p, r -= alpha q, partial r.z and r.r per
-//      virtual reduction block                                   -> grid barrier
-//   C  every CTA sums the partials in the same order and takes the same decision
-//      (beta, relative residual, replacement request, termination)
+//   A  tiles (round robin over CTAs): p = dinv r + beta p_old on the fly, q = A p, per-tile
+//      p_e . A_e p_e; the last tile to finish forms alpha = rho / p.Ap     -> grid barrier
+//   B  x += alpha p, r -= alpha q with r.z and r.r per reduction block; the last block to
+//      finish sums the blocks in order and updates the state (beta, relative residual,
+//      replacement request, termination)                                  -> grid barrier
 //
 // until the state asks for an FP64 residual replacement or terminates; the host then does
 // the replacement and launches again. The arithmetic and every summation order are those of
-// the two-kernel body (the same tile partial sum, the same kReduceBlocks x 256 partition of
-// the update reduction), so the iterates are bitwise identical to the graph and plain modes.
+// the graph body (same tile sum, same kReduceBlocks x 256 update partition), so the iterates
+// are bitwise identical to the graph and plain modes.
 //
-// Vectors written inside the launch by one CTA and read by another (r, p, q, the partial
-// sums) are read through L2 only (ld.global.cg). The barrier waits are bounded: a CTA that
+// Data written inside the launch by one CTA and read by another (r, p, q, partial sums, the
+// state) is read through L2 only (ld.global.cg). The barrier waits are bounded: a CTA that
 // waits longer than the limit flags the barrier, and the solve ends with
 // PCG_BARRIER_TIMEOUT instead of hanging.
 
@@ -60,18 +60,24 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, unsigned int& gen, int*
 template <int DIM, int KIND>
 __global__ void __launch_bounds__(kThreads) pcg_persistent_kernel(DevPlan P, PersistArgs A) {
   extern __shared__ __align__(32) unsigned char smem[];
-  __shared__ PcgState s_st;
   __shared__ double scratch[16];
-  __shared__ int s_flag;
+  __shared__ double s_beta, s_alpha;
+  __shared__ int s_stop, s_iter, s_flag;
   constexpr int OPS = OP_TANGENT | OP_PCG | OP_PERSIST;
-  const SmemLayout<float> L = smem_layout<float>(P.max_local, P.slot_cap, KIND == K_NH, true);
+  const SmemLayout<float> L = smem_layout<float>(P.max_local, P.slot_cap, P.step_cap, KIND == K_NH, true);
+  PcgState* st = A.st;
   unsigned int gen = 0;
+  auto read_state = [&]() {  // thread 0; the state was last written by another CTA
+    s_stop = (__ldcg(&st->done) != 0 || __ldcg(&st->repl) != 0) ? 1 : 0;
+    s_iter = __ldcg(&st->iter);
+    s_beta = __ldcg(&st->beta);
+  };
   if (threadIdx.x == 0) {
-    s_st = *A.st;
+    read_state();
     gen = cuda::atomic_ref<unsigned int, cuda::thread_scope_device>(A.bar->gen).load(cuda::memory_order_acquire);
   }
   __syncthreads();
-  if (s_st.done != 0 || s_st.repl != 0) return;  // uniform: written before the launch
+  if (s_stop) return;  // uniform: written before the launch
 
   OpArgs oa{};
   oa.u = A.u;
@@ -81,89 +87,52 @@ __global__ void __launch_bounds__(kThreads) pcg_persistent_kernel(DevPlan P, Per
   oa.pcg.dinv = A.dinv;
   oa.pcg.p[0] = A.p[0];
   oa.pcg.p[1] = A.p[1];
-  oa.pcg.st = A.st;
+  oa.pcg.st = st;
   oa.pcg.tile_part = A.tile_part;
+  oa.pcg.ticket = A.ticket;
   bool ok = true;
   for (;;) {
-    // ---- A: direction, q = A p, tile sums of p_e . A_e p_e
-    oa.pcg.beta = s_st.beta;
-    oa.pcg.odd = s_st.iter & 1;
+    // ---- A: direction, q = A p, tile sums of p_e . A_e p_e, alpha by the last tile
+    const int odd = s_iter & 1;
+    oa.pcg.beta = s_beta;
+    oa.pcg.odd = odd;
     for (int t = blockIdx.x; t < P.n_tiles; t += gridDim.x) {
       process_tile<DIM, KIND, OPS, double, float>(P, oa, t, smem, L);
       __syncthreads();
     }
     if (!(ok = grid_barrier(A.bar, gen, &s_flag))) break;
-
-    // ---- alpha = rho / p.Ap (the fused apply's last-tile sum, in every CTA)
-    {
-      double s = 0.0;
-      for (int i = threadIdx.x; i < P.n_tiles; i += blockDim.x) s += __ldcg(A.tile_part + i);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if ((threadIdx.x & 31) == 0) scratch[threadIdx.x >> 5] = s;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        double pap = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pap += scratch[w];
-        if (pap == 0.0 || !isfinite(pap)) {
-          s_st.alpha = 0.0;
-          s_st.done = isfinite(pap) ? PCG_BREAKDOWN : PCG_NONFINITE;
-        } else {
-          s_st.alpha = s_st.rho / pap;
-        }
-      }
-      __syncthreads();
-      if (s_st.done != 0) break;
+    if (threadIdx.x == 0) {
+      s_stop = __ldcg(&st->done) != 0 ? 1 : 0;
+      s_alpha = __ldcg(&st->alpha);
     }
+    __syncthreads();
+    if (s_stop) break;
 
-    // ---- B: x += alpha p, r -= alpha q; r.z and r.r partials of virtual block vb
+    // ---- B: x += alpha p, r -= alpha q; the last reduction block updates the state
     {
-      const double alpha = s_st.alpha;
-      const double* p = oa.pcg.odd ? A.p[0] : A.p[1];  // the direction just formed
+      const double alpha = s_alpha;
+      const double* p = odd ? A.p[0] : A.p[1];  // the direction just formed
       for (int vb = blockIdx.x; vb < kReduceBlocks; vb += gridDim.x) {
         double v[2] = {0.0, 0.0};
-        for (int64_t i = (int64_t)vb * kReduceThreads + threadIdx.x; i < A.n;
-             i += (int64_t)kReduceBlocks * kReduceThreads) {
-          A.x[i] += alpha * __ldcg(p + i);
-          const double ri = __ldcg(A.r + i) - alpha * __ldcg(A.q + i);
-          A.r[i] = ri;
-          v[0] += ri * (A.dinv[i] * ri);
-          v[1] += ri * ri;
-        }
-        block_sum<2>(v, scratch);
-        if (threadIdx.x == 0) {
-          A.red_part[vb * 2] = v[0];
-          A.red_part[vb * 2 + 1] = v[1];
-        }
+        pcg_update_range(A.n, A.x, A.r, p, A.q, A.dinv, alpha, vb, v);
+        if (grid_sum_v<2>(v, A.red_part, A.red_counter, scratch, vb, kReduceBlocks) && threadIdx.x == 0)
+          pcg_finish_update(st, v[0], v[1]);
       }
     }
     if (!(ok = grid_barrier(A.bar, gen, &s_flag))) break;
-
-    // ---- C: totals in block order, then the iteration's bookkeeping (same in every CTA)
-    {
-      double acc[2] = {0.0, 0.0};
-      for (int b = threadIdx.x; b < kReduceBlocks; b += blockDim.x) {
-        acc[0] += __ldcg(A.red_part + b * 2);
-        acc[1] += __ldcg(A.red_part + b * 2 + 1);
-      }
-      block_sum<2>(acc, scratch);
-      if (threadIdx.x == 0) pcg_finish_update(&s_st, acc[0], acc[1]);
-      __syncthreads();
-      if (s_st.done != 0 || s_st.repl != 0) break;
-    }
+    if (threadIdx.x == 0) read_state();
+    __syncthreads();
+    if (s_stop) break;
   }
-  if (threadIdx.x == 0) {
-    if (!ok && s_st.done == 0) s_st.done = PCG_BARRIER_TIMEOUT;
-    if (blockIdx.x == 0) *A.st = s_st;
-    if (!ok) cuda::atomic_ref<int, cuda::thread_scope_device>(A.st->done).store(PCG_BARRIER_TIMEOUT);
-  }
+  if (!ok && threadIdx.x == 0)
+    cuda::atomic_ref<int, cuda::thread_scope_device>(st->done).store(PCG_BARRIER_TIMEOUT);
 }
 
 template <int DIM, int KIND>
 static pfem_status run_persistent(const DevPlan& P, const PersistArgs& a, cudaStream_t s) {
   static int max_dyn = 0;  // per instantiation
   auto kern = pcg_persistent_kernel<DIM, KIND>;
-  const size_t smem = smem_layout<float>(P.max_local, P.slot_cap, KIND == K_NH, true).total;
+  const size_t smem = smem_layout<float>(P.max_local, P.slot_cap, P.step_cap, KIND == K_NH, true).total;
   pfem_status st = allow_dynamic_smem(kern, smem, &max_dyn);
   if (st) return st;
   int dev = 0, n_sm = 0, nb = 0;

@@ -10,7 +10,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
   extern __shared__ __align__(32) unsigned char smem[];
   constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
-  const SmemLayout<CT> L = smem_layout<CT>(P.max_local, P.slot_cap, NEED_U, NEED_V);
+  const SmemLayout<CT> L = smem_layout<CT>(P.max_local, P.slot_cap, P.step_cap, NEED_U, NEED_V);
   process_tile<DIM, KIND, OPS, VT, CT>(P, A, blockIdx.x, smem, L);
 }
 
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(kThreads) batch_kernel(BatchDev B, OpArgs A) {
   if (A.r) a.r = static_cast<float*>(A.r) + off;
   a.out_scale = B.mesh_scale ? B.mesh_scale + bt.x : nullptr;
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
-  const SmemLayout<float> L = smem_layout<float>(B.max_local, B.slot_cap, true, NEED_V);
+  const SmemLayout<float> L = smem_layout<float>(B.max_local, B.slot_cap, B.step_cap, true, NEED_V);
   if (sP.kind == PFEM_LINEAR) process_tile<3, K_LIN, OPS, float, float>(sP, a, bt.y, smem, L);
   else process_tile<3, K_NH, OPS, float, float>(sP, a, bt.y, smem, L);
 }
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) batch_energy_kernel(BatchDev B, const flo
 template <int OPS>
 static pfem_status run_batch(const BatchDev& B, const OpArgs& A, int n_blocks, cudaStream_t s) {
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
-  const SmemLayout<float> L = smem_layout<float>(B.max_local, B.slot_cap, true, NEED_V);
+  const SmemLayout<float> L = smem_layout<float>(B.max_local, B.slot_cap, B.step_cap, true, NEED_V);
   static int max_dyn = 0;
   pfem_status st = allow_dynamic_smem(batch_kernel<OPS>, L.total, &max_dyn);
   if (st) return st;
@@ -103,7 +103,7 @@ pfem_status launch_batch(const BatchDev& B, int n_blocks, int n_meshes, const fl
 // ---- serving: one shared PCG step over all resident solves ------------------------------
 
 __global__ void __launch_bounds__(kThreads) serve_apply_kernel(const ReqDev* reqs, const int2* btile, int max_local,
-                                                               int slot_cap) {
+                                                               int slot_cap, int step_cap) {
   extern __shared__ __align__(32) unsigned char smem[];
   __shared__ ReqDev sR;
   const int2 bt = btile[blockIdx.x];
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) serve_apply_kernel(const ReqDev* req
   a.y = sR.q;
   a.load_scale = 1.0;
   a.pcg = sR.pcg;
-  const SmemLayout<float> L = smem_layout<float>(max_local, slot_cap, true, true);
+  const SmemLayout<float> L = smem_layout<float>(max_local, slot_cap, step_cap, true, true);
   constexpr int OPS = OP_TANGENT | OP_PCG;
   if (sR.plan.kind == PFEM_LINEAR) process_tile<3, K_LIN, OPS, double, float>(sR.plan, a, bt.y, smem, L);
   else process_tile<3, K_NH, OPS, double, float>(sR.plan, a, bt.y, smem, L);
@@ -179,13 +179,13 @@ __global__ void __launch_bounds__(256) serve_update_kernel(const ReqDev* reqs, c
 }
 
 pfem_status launch_serve_step(const ReqDev* reqs, const int2* btile, int n_apply_blocks, const int* ublk,
-                              int n_update_blocks, int max_local, int slot_cap, cudaStream_t s) {
-  const SmemLayout<float> L = smem_layout<float>(max_local, slot_cap, true, true);
+                              int n_update_blocks, int max_local, int slot_cap, int step_cap, cudaStream_t s) {
+  const SmemLayout<float> L = smem_layout<float>(max_local, slot_cap, step_cap, true, true);
   static int max_dyn = 0;
   pfem_status st = allow_dynamic_smem(serve_apply_kernel, L.total, &max_dyn);
   if (st) return st;
   if (n_apply_blocks > 0) {
-    serve_apply_kernel<<<n_apply_blocks, kThreads, L.total, s>>>(reqs, btile, max_local, slot_cap);
+    serve_apply_kernel<<<n_apply_blocks, kThreads, L.total, s>>>(reqs, btile, max_local, slot_cap, step_cap);
     PFEM_COUNT_LAUNCH();
   }
   if (n_update_blocks > 0) {
@@ -200,7 +200,7 @@ template <int DIM, int KIND, int OPS, typename VT, typename CT>
 static pfem_status run(const DevPlan& P, const OpArgs& A, cudaStream_t s) {
   constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
-  const SmemLayout<CT> L = smem_layout<CT>(P.max_local, P.slot_cap, NEED_U, NEED_V);
+  const SmemLayout<CT> L = smem_layout<CT>(P.max_local, P.slot_cap, P.step_cap, NEED_U, NEED_V);
   if (P.n_tiles <= 0) return PFEM_OK;
   static int max_dyn = 0;  // per instantiation
   pfem_status st = allow_dynamic_smem(tile_kernel<DIM, KIND, OPS, VT, CT>, L.total, &max_dyn);
@@ -249,8 +249,8 @@ pfem_status launch_element_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dty
 size_t element_op_smem(const DevPlan& P, int ops, pfem_dtype ct) {
   const bool need_u = (ops & (OP_RESIDUAL | OP_ENERGY)) || (P.kind == PFEM_NEOHOOKEAN && (ops & (OP_TANGENT | OP_DIAG)));
   const bool need_v = (ops & OP_TANGENT) != 0;
-  if (ct == PFEM_F32) return smem_layout<float>(P.max_local, P.slot_cap, need_u, need_v).total;
-  return smem_layout<double>(P.max_local, P.slot_cap, need_u, need_v).total;
+  if (ct == PFEM_F32) return smem_layout<float>(P.max_local, P.slot_cap, P.step_cap, need_u, need_v).total;
+  return smem_layout<double>(P.max_local, P.slot_cap, P.step_cap, need_u, need_v).total;
 }
 
 }  // namespace pfem

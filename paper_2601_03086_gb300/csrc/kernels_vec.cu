@@ -91,13 +91,7 @@ __global__ void __launch_bounds__(kReduceThreads)
   const double alpha = st->alpha;
   const double* p = ((st->iter + 1) & 1) ? p1 : p0;
   double v[2] = {0.0, 0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] += alpha * p[i];
-    const double ri = r[i] - alpha * q[i];
-    r[i] = ri;
-    v[0] += ri * (dinv[i] * ri);
-    v[1] += ri * ri;
-  }
+  pcg_update_range(n, x, r, p, q, dinv, alpha, blockIdx.x, v);  // launched as kReduceBlocks x kReduceThreads
   if (grid_sum<2>(v, partials, counter, scratch) && threadIdx.x == 0) {
     pcg_finish_update(st, v[0], v[1]);
     if (set_cond) cudaGraphSetConditional(cond, (st->done == 0 && st->repl == 0) ? 1u : 0u);

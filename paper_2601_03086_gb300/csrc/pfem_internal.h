@@ -3,25 +3,33 @@
 // Data layout (device, per mesh)
 //   Elements are reordered along a Morton curve of their centroids and cut into tiles of at
 //   most kTileElems elements touching at most kTileNodes distinct nodes. A tile is the unit
-//   of work of one CTA: its nodes are staged in shared memory, every element of the tile is
-//   evaluated once, its corner contributions land in per-incidence shared-memory slots, and
-//   each tile node sums its slots in a fixed order (ascending element position, so the sum
-//   is bitwise reproducible without float atomics).
+//   of work of one CTA: its nodes are staged in shared memory and its elements are grouped
+//   into fans, one fan per thread. A fan is a chain of k <= kMaxFan simplices around a common
+//   hinge (an edge in 3-D, a vertex in 2-D) with ring nodes r_0..r_k; simplex i has the
+//   corners (hinge, r_i, r_{i+1}) and consecutive simplices share the face (hinge, r_{i+1}).
+//   The thread walks the ring once: every ring node is read once, its contributions from the
+//   two simplices that touch it are summed in registers, and it is written once to its own
+//   shared-memory slot; the hinge nodes accumulate over the whole fan. Each tile node then
+//   sums its slots in a fixed order (rank order), so the result is bitwise reproducible
+//   without float atomics.
 //   A node whose incident elements all lie in one tile ("complete") is written directly by
 //   that tile. A node shared by several tiles ("halo") gets one partial per tile, written to
-//   a scratch buffer; a second pass sums each halo node's partials in ascending tile order.
+//   a scratch buffer, and the last tile to publish one sums them in ascending tile order.
 //
-//   tile_a[t]  = {elem_begin, n_elem, lnode_begin, n_local}
-//   tile_b[t]  = {n_complete, partial_begin, 0, 0}
-//   lnode_f[l] = {x - x_anchor, y - y_anchor, z - z_anchor, info}  (float4; info bits below)
-//   lnode_d[l] = same coordinates in double (for the FP64 instantiation)
-//   slot_off[l]= first incidence slot of the tile node (uint16; the tile's slots run
-//                [0, n_elem*nv); a node's in-tile degree is slot_off[l+1]-slot_off[l], the
-//                last node's end is n_elem*nv)
-//   ecode[e]   = 4 x uint16 per element: local node index (bits 0-9) | rank (bits 10-15),
-//                rank = position of this incidence among the node's incidences in the tile
-//   emat_f/d[e]= (mu, lambda) per element (linear (E, nu) converted on the host)
-//   info       = node id (bits 0-27) | Dirichlet mask of DOF i at bit 28+i
+//   tile_a[t]   = {fan_begin, n_fans, lnode_begin, n_local}
+//   tile_b[t]   = {n_complete, partial_begin, step_begin, n_steps (= elements)}
+//   tile_cnt[t] = kMaxFan x uint16: cnt_i = fans of the tile with more than i simplices
+//                 (fans are sorted by length, longest first, so these are fans 0..cnt_i-1)
+//   lnode_f[l]  = {x - x_anchor, y - y_anchor, z - z_anchor, info}  (float4; info bits below)
+//   lnode_d[l]  = same coordinates in double (for the FP64 instantiation)
+//   slot_off[l] = first slot of the tile node (uint16; a node's slot count is
+//                 slot_off[l+1]-slot_off[l], the last node's end is the tile's slot count)
+//   fan_head[f] = {h_0, h_1 (3-D), r_0, k} codes: local node index (bits 0-9) | rank
+//                 (bits 10-15), rank = position of the incidence among the node's slots
+//   step_code[s], step_mat_f/d[s]: code of r_{i+1} and (mu, lambda) of simplex i of fan f,
+//                 stored step-major inside the tile: s = step_begin + sum_{j<i} cnt_j + f,
+//                 so a warp's fans read consecutive records at every step
+//   info        = node id (bits 0-27) | Dirichlet mask of DOF i at bit 28+i
 //   halo_info[h], halo_ptr[h..h+1], halo_src[k]: halo nodes (sorted by id) and the indices
 //                of their partials in ascending tile order
 #pragma once
@@ -40,7 +48,8 @@ struct __align__(32) PfemDouble4 {
   double x, y, z, w;
 };
 
-constexpr int kTileElems = 1024;   // max elements per tile
+constexpr int kTileElems = 2048;   // max elements per tile
+constexpr int kMaxFan = 8;         // max simplices per fan
 constexpr int kTileNodes = 1024;   // max distinct nodes per tile (10-bit local index)
 constexpr int kMaxRank = 63;       // max incidences of one node inside one tile (6 bits)
 constexpr int kInfoIdBits = 28;
@@ -73,14 +82,18 @@ struct HostPlan {
   std::vector<float> lnode_f;     // 4 per local node
   std::vector<double> lnode_d;    // 4 per local node
   std::vector<uint16_t> slot_off; // 1 per local node
-  std::vector<uint16_t> ecode;    // 4 per element
-  std::vector<float> emat_f;      // 2 per element
-  std::vector<double> emat_d;     // 2 per element
+  std::vector<uint16_t> tile_cnt; // kMaxFan per tile
+  std::vector<uint16_t> fan_head; // 4 per fan
+  std::vector<uint16_t> step_code;// 1 per step (element)
+  std::vector<float> step_mat_f;  // 2 per step
+  std::vector<double> step_mat_d; // 2 per step
+  int max_slots = 0;              // largest tile slot count
+  int64_t n_fans = 0;
   std::vector<int32_t> halo_info; // 1 per halo node
   std::vector<int32_t> halo_ptr;  // n_halo + 1
   std::vector<int32_t> halo_src;  // n_partials
   int64_t n_partials = 0;
-  std::vector<int32_t> elem_perm; // original element id at each tile-order position
+  std::vector<int32_t> elem_perm; // original element id of each step
   std::vector<int32_t> partial_halo; // halo node index of each partial
   int64_t n_tiles() const { return (int64_t)tile_a.size() / 4; }
   int64_t n_local() const { return (int64_t)slot_off.size(); }
@@ -109,7 +122,8 @@ struct DevPlan {
   int n_tiles;
   int n_halo;
   int max_local;         // largest tile node count (shared-memory sizing)
-  int slot_cap;          // largest tile incidence count = max tile elements * (dim + 1)
+  int slot_cap;          // largest tile slot count
+  int step_cap;          // largest tile element (step) count
   int64_t n_nodes;
   int64_t n_partials;
   const int4* tile_a;
@@ -117,9 +131,11 @@ struct DevPlan {
   const float4* lnode_f;
   const PfemDouble4* lnode_d;
   const uint16_t* slot_off;
-  const ushort4* ecode;
-  const float2* emat_f;
-  const double2* emat_d;
+  const uint4* tile_cnt;   // kMaxFan uint16 per tile
+  const ushort4* fan_head;
+  const uint16_t* step_code;
+  const float2* step_mat_f;
+  const double2* step_mat_d;
   const int32_t* halo_info;
   const int32_t* halo_ptr;
   const int32_t* halo_src;
@@ -152,6 +168,7 @@ enum : int {
   PCG_NONFINITE = 3,
   PCG_BREAKDOWN = 4,
   PCG_BARRIER_TIMEOUT = 6,  // a grid barrier of the persistent kernel gave up waiting
+  PCG_STAGNATED = 7,        // the FP64 true residual stopped decreasing between replacements
 };
 
 // Device-resident scalars of one Jacobi-PCG solve (FP64).
@@ -207,7 +224,9 @@ struct PersistArgs {
   double* q;
   PcgState* st;
   double* tile_part;    // n_tiles doubles
+  unsigned int* ticket; // last-tile ticket of the apply (zero; reset by its user)
   double* red_part;     // kReduceBlocks * 2 doubles
+  unsigned int* red_counter;  // last-block ticket of the update (zero; reset by its user)
   GridBar* bar;
   int64_t n;            // DOFs
 };
@@ -231,7 +250,8 @@ struct BatchDev {
   const int64_t* dof_off;  // n_meshes + 1 DOF offsets into the concatenated vectors
   const float* mesh_scale; // n_meshes upstream factors for grad / hvp (null = 1)
   int max_local;           // largest tile node count over the batch
-  int slot_cap;            // largest tile incidence count over the batch
+  int slot_cap;            // largest tile slot count over the batch
+  int step_cap;            // largest tile element count over the batch
 };
 
 pfem_status launch_batch(const BatchDev& B, int n_blocks, int n_meshes, const float* u, const float* v, float* grad,
@@ -255,7 +275,7 @@ struct ReqDev {
 // Shared PCG step over many solves: fused apply (one CTA per (solve, tile)) then update
 // (one CTA range per solve). btile: (solve, tile) per apply block; ublk: solve per update block.
 pfem_status launch_serve_step(const ReqDev* reqs, const int2* btile, int n_apply_blocks, const int* ublk,
-                              int n_update_blocks, int max_local, int slot_cap, cudaStream_t s);
+                              int n_update_blocks, int max_local, int slot_cap, int step_cap, cudaStream_t s);
 
 // Blocks the update launch gives a solve of n DOFs (depends on n only).
 inline int serve_update_blocks(int64_t n) {

@@ -65,15 +65,162 @@ static bool finite_all(const double* p, int64_t n) {
   return true;
 }
 
-// Tile size: 512 elements once the mesh fills the GPU several times over (fewer halo
-// partials per element); smaller tiles for small meshes so that at least ~8 tiles land on
-// each of the 152 SMs (latency hiding beats halo overhead there).
+// Tile size: 1024 elements once the mesh fills the GPU several times over (longer fans and
+// fewer halo partials per element); smaller tiles for small meshes so that at least ~4 tiles
+// land on each of the 152 SMs.
 int default_tile_elems(int64_t n_elems) {
-  const int64_t per = (n_elems + 152 * 8 - 1) / (152 * 8);
+  const int64_t per = (n_elems + 152 * 4 - 1) / (152 * 4);
   int64_t t = (per + 63) / 64 * 64;
-  if (t < 128) t = 128;
-  if (t > 512) t = 512;
+  if (t < 256) t = 256;
+  if (t > 1024) t = 1024;
   return (int)t;
+}
+
+// One fan (see pfem_internal.h): hinge and ring as tile-local node indices, and the keyed
+// positions of its simplices (simplex i spans hinge, ring[i], ring[i+1]).
+struct Fan {
+  int h[2] = {0, 0};
+  int ring[kMaxFan + 1];
+  int64_t pos[kMaxFan];
+  int k = 0;
+};
+
+constexpr int kFanCap = kMaxFan;  // longest fan the planner builds
+
+// Greedy fans over the elements at keyed positions [b, e) (one tile). Elements are taken in
+// order; each unassigned element tries every hinge (edge in 3-D, vertex in 2-D), walks both
+// ways around it through face-adjacent unassigned elements of the tile, and keeps the
+// longest chain (first hinge on ties, at most kFanCap simplices).
+static void build_fans(const pfem_mesh_desc* d, int nv, const std::vector<std::pair<uint64_t, int32_t>>& keyed,
+                       int64_t b, int64_t e, const std::vector<int32_t>& lmap, std::vector<Fan>& fans) {
+  const int ne = (int)(e - b);
+  const int hs = nv - 2;  // hinge size
+  std::vector<int> L((size_t)ne * 4, 0);
+  for (int j = 0; j < ne; ++j) {
+    const int32_t* c = d->conn + (int64_t)keyed[(size_t)(b + j)].second * nv;
+    for (int a = 0; a < nv; ++a) L[(size_t)j * 4 + a] = lmap[c[a]];
+  }
+  // face adjacency inside the tile: nb[j*4+o] = element across the face opposite corner o
+  std::vector<std::pair<uint32_t, int32_t>> faces;
+  faces.reserve((size_t)ne * nv);
+  for (int j = 0; j < ne; ++j)
+    for (int o = 0; o < nv; ++o) {
+      int f[3], m = 0;
+      for (int a = 0; a < nv; ++a)
+        if (a != o) f[m++] = L[(size_t)j * 4 + a];
+      std::sort(f, f + m);
+      uint32_t key = 0;
+      for (int i = 0; i < m; ++i) key |= (uint32_t)f[i] << (10 * i);
+      faces.push_back({key, j * 4 + o});
+    }
+  std::sort(faces.begin(), faces.end());
+  std::vector<int> nb((size_t)ne * 4, -1);
+  for (size_t i = 0; i + 1 < faces.size(); ++i)
+    if (faces[i].first == faces[i + 1].first) {
+      nb[(size_t)faces[i].second] = faces[i + 1].second >> 2;
+      nb[(size_t)faces[i + 1].second] = faces[i].second >> 2;
+      ++i;
+    }
+  std::vector<char> used((size_t)ne, 0);
+  auto corner_of = [&](int j, int node) {
+    for (int a = 0; a < nv; ++a)
+      if (L[(size_t)j * 4 + a] == node) return a;
+    return -1;
+  };
+  // walks from element j, leaving ring node `from` behind and entering `to`, up to `room`
+  // simplices; appends (element, apex) pairs
+  auto walk = [&](int j, const int* hinge, int from, int to, int room, const int* chain, int n_chain,
+                  int* els, int* apex) {
+    int n = 0;
+    while (n < room) {
+      const int o = corner_of(j, from);
+      const int nj = o < 0 ? -1 : nb[(size_t)j * 4 + o];
+      if (nj < 0 || used[(size_t)nj]) break;
+      bool dup = false;
+      for (int i = 0; i < n_chain && !dup; ++i) dup = chain[i] == nj;
+      for (int i = 0; i < n && !dup; ++i) dup = els[i] == nj;
+      if (dup) break;
+      int ap = -1;
+      for (int a = 0; a < nv; ++a) {
+        const int x = L[(size_t)nj * 4 + a];
+        bool in = x == to;
+        for (int h = 0; h < hs; ++h) in = in || x == hinge[h];
+        if (!in) ap = x;
+      }
+      if (ap < 0) break;
+      els[n] = nj;
+      apex[n] = ap;
+      ++n;
+      from = to;
+      to = ap;
+      j = nj;
+    }
+    return n;
+  };
+  for (int j = 0; j < ne; ++j) {
+    if (used[(size_t)j]) continue;
+    int best = -1, best_nf = 0, best_nb = 0, bf_el[kMaxFan], bf_ap[kMaxFan], bb_el[kMaxFan], bb_ap[kMaxFan];
+    int best_h[2] = {0, 0}, best_c = 0, best_d = 0;
+    const int* Lj = &L[(size_t)j * 4];
+    const int n_hinges = nv == 4 ? 6 : 3;
+    static const int kPairs[6][4] = {{0, 1, 2, 3}, {0, 2, 1, 3}, {0, 3, 1, 2}, {1, 2, 0, 3}, {1, 3, 0, 2}, {2, 3, 0, 1}};
+    static const int kVerts[3][3] = {{0, 1, 2}, {1, 0, 2}, {2, 0, 1}};
+    for (int hc = 0; hc < n_hinges; ++hc) {
+      int hinge[2], c, dd;
+      if (nv == 4) {
+        hinge[0] = Lj[kPairs[hc][0]];
+        hinge[1] = Lj[kPairs[hc][1]];
+        c = Lj[kPairs[hc][2]];
+        dd = Lj[kPairs[hc][3]];
+      } else {
+        hinge[0] = Lj[kVerts[hc][0]];
+        hinge[1] = -1;
+        c = Lj[kVerts[hc][1]];
+        dd = Lj[kVerts[hc][2]];
+      }
+      int f_el[kMaxFan], f_ap[kMaxFan], b_el[kMaxFan], b_ap[kMaxFan];
+      const int nf = walk(j, hinge, c, dd, kFanCap - 1, &j, 1, f_el, f_ap);
+      int chain[kMaxFan + 1];
+      chain[0] = j;
+      for (int i = 0; i < nf; ++i) chain[i + 1] = f_el[i];
+      const int nbk = walk(j, hinge, dd, c, kFanCap - 1 - nf, chain, nf + 1, b_el, b_ap);
+      if (1 + nf + nbk > best) {
+        best = 1 + nf + nbk;
+        best_nf = nf;
+        best_nb = nbk;
+        std::copy(f_el, f_el + nf, bf_el);
+        std::copy(f_ap, f_ap + nf, bf_ap);
+        std::copy(b_el, b_el + nbk, bb_el);
+        std::copy(b_ap, b_ap + nbk, bb_ap);
+        best_h[0] = hinge[0];
+        best_h[1] = hinge[1];
+        best_c = c;
+        best_d = dd;
+      }
+    }
+    Fan F;
+    F.h[0] = best_h[0];
+    F.h[1] = best_h[1] < 0 ? 0 : best_h[1];
+    int r = 0, k = 0;
+    for (int i = best_nb - 1; i >= 0; --i) {  // backward chain, outermost first
+      F.ring[r++] = bb_ap[i];
+      F.pos[k++] = b + bb_el[i];
+      used[(size_t)bb_el[i]] = 1;
+    }
+    F.ring[r++] = best_c;
+    F.ring[r++] = best_d;
+    F.pos[k++] = b + j;
+    used[(size_t)j] = 1;
+    for (int i = 0; i < best_nf; ++i) {
+      F.ring[r++] = bf_ap[i];
+      F.pos[k++] = b + bf_el[i];
+      used[(size_t)bf_el[i]] = 1;
+    }
+    F.k = k;
+    fans.push_back(F);
+  }
+  // longest first (stable: equal lengths keep the element order)
+  std::stable_sort(fans.begin(), fans.end(), [](const Fan& x, const Fan& y) { return x.k > y.k; });
 }
 
 pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>* f_ext, int tile_elems) {
@@ -217,9 +364,14 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
   P->lnode_f.clear();
   P->lnode_d.clear();
   P->slot_off.clear();
-  P->ecode.assign((size_t)E * 4, 0);
-  P->emat_f.assign((size_t)E * 2, 0.f);
-  P->emat_d.assign((size_t)E * 2, 0.0);
+  P->tile_cnt.clear();
+  P->fan_head.clear();
+  P->step_code.assign((size_t)E, 0);
+  P->step_mat_f.assign((size_t)E * 2, 0.f);
+  P->step_mat_d.assign((size_t)E * 2, 0.0);
+  P->elem_perm.assign((size_t)E, 0);
+  P->n_fans = 0;
+  P->max_slots = 0;
   P->max_local = 0;
   P->max_elems = 0;
   std::vector<int32_t> stamp((size_t)N, -1), tdeg((size_t)N, 0), lmap((size_t)N, 0), rk;
@@ -230,6 +382,9 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
   int32_t tile = 0;
   int64_t tbegin = 0;
 
+  std::vector<Fan> fans;
+  std::vector<int32_t> fdeg;
+
   auto close_tile = [&](int64_t tend) {
     comp.clear();
     halo.clear();
@@ -239,7 +394,6 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
     const int n_local = (int)(comp.size() + halo.size());
     const int64_t lbeg = P->n_local();
     int li = 0;
-    int off = 0;
     const int32_t anchor = comp.empty() ? halo[0] : comp[0];
     auto push = [&](int32_t n) {
       lmap[n] = li++;
@@ -255,36 +409,64 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
       std::memcpy(&d4[3], &inf, 4);
       P->lnode_f.insert(P->lnode_f.end(), f4, f4 + 4);
       P->lnode_d.insert(P->lnode_d.end(), d4, d4 + 4);
-      P->slot_off.push_back((uint16_t)off);
-      off += tdeg[n];
     };
     for (int32_t n : comp) push(n);
     for (int32_t n : halo) push(n);
-    rk.assign((size_t)n_local, 0);
-    for (int64_t p = tbegin; p < tend; ++p) {
-      const int32_t e = keyed[(size_t)p].second;
-      const int32_t* c = d->conn + (int64_t)e * nv;
-      for (int a = 0; a < nv; ++a) {
-        const int l = lmap[c[a]];
-        const int r = rk[l]++;
-        P->ecode[(size_t)p * 4 + a] = (uint16_t)(l | (r << 10));
-      }
-      double a_ = d->mat_a[e], b_ = d->mat_b[e], mu, lam;
-      if (d->kind == PFEM_LINEAR) {
-        mu = a_ / (2.0 * (1.0 + b_));
-        lam = a_ * b_ / ((1.0 + b_) * (1.0 - 2.0 * b_));
-      } else {
-        mu = a_;
-        lam = b_;
-      }
-      P->emat_d[(size_t)p * 2] = mu;
-      P->emat_d[(size_t)p * 2 + 1] = lam;
-      P->emat_f[(size_t)p * 2] = (float)mu;
-      P->emat_f[(size_t)p * 2 + 1] = (float)lam;
+
+    // fans, slots per node (one per fan the node belongs to, per ring position), ranks
+    fans.clear();
+    if (tend > tbegin) build_fans(d, nv, keyed, tbegin, tend, lmap, fans);
+    const int hs = nv - 2;
+    fdeg.assign((size_t)n_local, 0);
+    for (const Fan& F : fans) {
+      for (int h = 0; h < hs; ++h) fdeg[(size_t)F.h[h]]++;
+      for (int i = 0; i <= F.k; ++i) fdeg[(size_t)F.ring[i]]++;
     }
+    int off = 0;
+    for (int l = 0; l < n_local; ++l) {
+      P->slot_off.push_back((uint16_t)off);
+      off += fdeg[(size_t)l];
+    }
+    P->max_slots = std::max(P->max_slots, off);
+    rk.assign((size_t)n_local, 0);
+    auto code = [&](int l) { return (uint16_t)(l | (rk[(size_t)l]++ << 10)); };
+    int cnt[kMaxFan] = {0};
+    for (const Fan& F : fans)
+      for (int i = 0; i < F.k; ++i) cnt[i]++;
+    int base[kMaxFan] = {0};
+    for (int i = 1; i < kMaxFan; ++i) base[i] = base[i - 1] + cnt[i - 1];
+    for (int i = 0; i < kMaxFan; ++i) P->tile_cnt.push_back((uint16_t)cnt[i]);
+    const int64_t fan_beg = P->n_fans;
+    for (size_t f = 0; f < fans.size(); ++f) {
+      const Fan& F = fans[f];
+      const uint16_t h0 = code(F.h[0]);
+      const uint16_t h1 = hs == 2 ? code(F.h[1]) : (uint16_t)0;
+      const uint16_t r0 = code(F.ring[0]);
+      const uint16_t head[4] = {h0, h1, r0, (uint16_t)F.k};
+      P->fan_head.insert(P->fan_head.end(), head, head + 4);
+      for (int i = 0; i < F.k; ++i) {
+        const size_t st = (size_t)(tbegin + base[i] + (int64_t)f);
+        P->step_code[st] = code(F.ring[i + 1]);
+        const int32_t e = keyed[(size_t)F.pos[i]].second;
+        P->elem_perm[st] = e;
+        double a_ = d->mat_a[e], b_ = d->mat_b[e], mu, lam;
+        if (d->kind == PFEM_LINEAR) {
+          mu = a_ / (2.0 * (1.0 + b_));
+          lam = a_ * b_ / ((1.0 + b_) * (1.0 - 2.0 * b_));
+        } else {
+          mu = a_;
+          lam = b_;
+        }
+        P->step_mat_d[st * 2] = mu;
+        P->step_mat_d[st * 2 + 1] = lam;
+        P->step_mat_f[st * 2] = (float)mu;
+        P->step_mat_f[st * 2 + 1] = (float)lam;
+      }
+    }
+    P->n_fans += (int64_t)fans.size();
     for (size_t j = 0; j < halo.size(); ++j) halo_pairs.push_back({halo[j], (int32_t)(n_partials + (int64_t)j)});
-    const int32_t ta[4] = {(int32_t)tbegin, (int32_t)(tend - tbegin), (int32_t)lbeg, n_local};
-    const int32_t tb[4] = {(int32_t)comp.size(), (int32_t)n_partials, 0, 0};
+    const int32_t ta[4] = {(int32_t)fan_beg, (int32_t)fans.size(), (int32_t)lbeg, n_local};
+    const int32_t tb[4] = {(int32_t)comp.size(), (int32_t)n_partials, (int32_t)tbegin, (int32_t)(tend - tbegin)};
     P->tile_a.insert(P->tile_a.end(), ta, ta + 4);
     P->tile_b.insert(P->tile_b.end(), tb, tb + 4);
     n_partials += (int64_t)halo.size();
@@ -375,8 +557,6 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
   }
   if (d->f_ext_extra)
     for (int64_t i = 0; i < N * dim; ++i) (*f_ext)[(size_t)i] += d->f_ext_extra[i];
-  P->elem_perm.resize((size_t)E);
-  for (int64_t p = 0; p < E; ++p) P->elem_perm[(size_t)p] = keyed[(size_t)p].second;
   return PFEM_OK;
 }
 
@@ -396,56 +576,106 @@ pfem_status verify_plan(const pfem_mesh_desc* d, const HostPlan& P) {
   std::vector<int32_t> owner((size_t)N, -1), partial_tiles((size_t)N, 0), partial_deg((size_t)N, 0);
   std::vector<int64_t> partial_node((size_t)std::max<int64_t>(P.n_partials, 1), -1), partial_deg_of;
   partial_deg_of.assign((size_t)std::max<int64_t>(P.n_partials, 1), 0);
-  int64_t next_e = 0;
+  int64_t next_e = 0, next_f = 0;
+  std::vector<char> elem_seen((size_t)std::max<int64_t>(E, 1), 0);
+  const int hs = nv - 2;
   for (int64_t t = 0; t < T; ++t) {
     const int32_t* ta = &P.tile_a[(size_t)t * 4];
     const int32_t* tb = &P.tile_b[(size_t)t * 4];
-    const int eb = ta[0], ne = ta[1], lb = ta[2], nl = ta[3], nc = tb[0], pb = tb[1];
-    if (eb != next_e || ne < 0 || (ne == 0 && eb != E)) return bad("tiles must cover elements contiguously", t, eb);
-    next_e = eb + ne;
+    const int fb = ta[0], nf = ta[1], lb = ta[2], nl = ta[3], nc = tb[0], pb = tb[1], sb = tb[2], ns = tb[3];
+    if (sb != next_e || ns < 0) return bad("tiles must cover elements contiguously", t, sb);
+    if (fb != next_f || nf < 0) return bad("tiles must cover fans contiguously", t, fb);
+    next_e = sb + ns;
+    next_f = fb + nf;
     if (nl < 1 || nl > kTileNodes || nc > nl) return bad("tile node count", t, nl);
-    std::vector<int> seen((size_t)ne * nv, 0), next_rank((size_t)nl, 0);
+    const uint16_t* cnt = &P.tile_cnt[(size_t)t * kMaxFan];
+    int base[kMaxFan + 1] = {0};
+    for (int i = 0; i < kMaxFan; ++i) {
+      if (i > 0 && cnt[i] > cnt[i - 1]) return bad("fan counts not non-increasing", t, i);
+      base[i + 1] = base[i] + cnt[i];
+    }
+    if (base[kMaxFan] != ns || (nf > 0 && cnt[0] != nf) || (nf == 0 && ns != 0)) return bad("fan counts", t, ns);
+    int total_slots = 0;
+    std::vector<int> node_slots((size_t)nl, 0), next_rank((size_t)nl, 0), inc((size_t)nl, 0);
+    for (int f = 0; f < nf; ++f) {
+      const uint16_t* hd = &P.fan_head[(size_t)(fb + f) * 4];
+      total_slots += hs + hd[3] + 1;
+    }
     for (int l = 0; l < nl; ++l) {
       const int off = P.slot_off[(size_t)(lb + l)];
-      const int end = l + 1 < nl ? P.slot_off[(size_t)(lb + l + 1)] : ne * nv;
+      const int end = l + 1 < nl ? P.slot_off[(size_t)(lb + l + 1)] : total_slots;
       if (end < off) return bad("slot offsets not monotone", t, l);
+      node_slots[(size_t)l] = end - off;
     }
-    for (int e = 0; e < ne; ++e) {
-      const int32_t orig = P.elem_perm[(size_t)(eb + e)];
-      for (int a = 0; a < nv; ++a) {
-        const uint16_t code = P.ecode[(size_t)(eb + e) * 4 + a];
-        const int l = code & 1023, r = code >> 10;
-        if (l >= nl) return bad("local index out of range", t, l);
-        int32_t info;
-        std::memcpy(&info, &P.lnode_f[(size_t)(lb + l) * 4 + 3], 4);
-        const int64_t gid = (int64_t)((uint32_t)info & kInfoIdMask);
-        if (gid != d->conn[(int64_t)orig * nv + a]) return bad("corner code points at the wrong node", orig, a);
-        if (r != next_rank[l]++) return bad("ranks not in element order", t, l);
-        const int off = P.slot_off[(size_t)(lb + l)];
-        const int end = l + 1 < nl ? P.slot_off[(size_t)(lb + l + 1)] : ne * nv;
-        if (off + r >= end) return bad("rank beyond the node's slot range", t, l);
-        if (seen[(size_t)(off + r)]++) return bad("slot used twice", t, off + r);
-      }
-    }
-    for (int l = 0; l < nl; ++l) {
+    std::vector<int> seen((size_t)std::max(total_slots, 1), 0);
+    auto gid_of = [&](int l) {
       int32_t info;
       std::memcpy(&info, &P.lnode_f[(size_t)(lb + l) * 4 + 3], 4);
-      const int64_t gid = (int64_t)((uint32_t)info & kInfoIdMask);
+      return (int64_t)((uint32_t)info & kInfoIdMask);
+    };
+    auto take = [&](uint16_t code, int* l_out) -> bool {
+      const int l = code & 1023, r = code >> 10;
+      if (l >= nl) return false;
+      if (r != next_rank[(size_t)l]++) return false;
+      const int off = P.slot_off[(size_t)(lb + l)];
+      if (r >= node_slots[(size_t)l]) return false;
+      if (seen[(size_t)(off + r)]++) return false;
+      *l_out = l;
+      return true;
+    };
+    for (int f = 0; f < nf; ++f) {
+      const uint16_t* hd = &P.fan_head[(size_t)(fb + f) * 4];
+      const int k = hd[3];
+      if (k < 1 || k > kMaxFan) return bad("fan length", t, k);
+      if (f > 0 && k > P.fan_head[(size_t)(fb + f - 1) * 4 + 3]) return bad("fans not sorted by length", t, f);
+      int hl[2] = {0, 0}, rprev = 0;
+      if (!take(hd[0], &hl[0])) return bad("hinge code", t, f);
+      if (hs == 2 && !take(hd[1], &hl[1])) return bad("hinge code", t, f);
+      if (!take(hd[2], &rprev)) return bad("ring code", t, f);
+      for (int i = 0; i < k; ++i) {
+        const int64_t st = sb + base[i] + f;
+        if (f >= cnt[i]) return bad("fan step outside its count", t, f);
+        int rnext = 0;
+        if (!take(P.step_code[(size_t)st], &rnext)) return bad("ring code", t, f);
+        const int32_t orig = P.elem_perm[(size_t)st];
+        if (orig < 0 || orig >= E || elem_seen[(size_t)orig]++) return bad("element missing or repeated", orig, st);
+        int64_t want[4];
+        int m = 0;
+        for (int h = 0; h < hs; ++h) want[m++] = gid_of(hl[h]);
+        want[m++] = gid_of(rprev);
+        want[m++] = gid_of(rnext);
+        int64_t have[4];
+        for (int a = 0; a < nv; ++a) have[a] = d->conn[(int64_t)orig * nv + a];
+        std::sort(want, want + nv);
+        std::sort(have, have + nv);
+        for (int a = 0; a < nv; ++a)
+          if (want[a] != have[a]) return bad("simplex corners do not match the element", orig, a);
+        for (int h = 0; h < hs; ++h) inc[(size_t)hl[h]]++;
+        inc[(size_t)rprev]++;
+        inc[(size_t)rnext]++;
+        rprev = rnext;
+      }
+    }
+    for (int l = 0; l < nl; ++l)
+      if (next_rank[(size_t)l] != node_slots[(size_t)l]) return bad("node slots not all used", t, l);
+    for (int l = 0; l < nl; ++l) {
+      const int64_t gid = gid_of(l);
       if (l < nc) {
-        if (next_rank[l] != gdeg[(size_t)gid]) return bad("complete node misses incidences", gid, next_rank[l]);
+        if (inc[(size_t)l] != gdeg[(size_t)gid]) return bad("complete node misses incidences", gid, inc[(size_t)l]);
         if (owner[(size_t)gid] != -1) return bad("node complete in two tiles", gid, t);
         owner[(size_t)gid] = (int32_t)t;
       } else {
         const int64_t pi = pb + (l - nc);
         if (pi >= P.n_partials) return bad("partial index out of range", t, pi);
         partial_node[(size_t)pi] = gid;
-        partial_deg_of[(size_t)pi] = next_rank[l];
+        partial_deg_of[(size_t)pi] = inc[(size_t)l];
         partial_tiles[(size_t)gid]++;
-        partial_deg[(size_t)gid] += next_rank[l];
+        partial_deg[(size_t)gid] += inc[(size_t)l];
       }
     }
   }
   if (next_e != E) return bad("tiles do not cover all elements", next_e, E);
+  if (next_f != P.n_fans) return bad("tiles do not cover all fans", next_f, P.n_fans);
   std::vector<int> listed((size_t)N, 0);
   for (int64_t h = 0; h < P.n_halo(); ++h) {
     const int64_t gid = (int64_t)((uint32_t)P.halo_info[(size_t)h] & kInfoIdMask);

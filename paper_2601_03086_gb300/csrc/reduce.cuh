@@ -33,18 +33,20 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double* scratch /* >= 
     }
 }
 
-// Publishes this block's N partials and returns true in every thread of the last block,
-// whose thread-0 `v` then holds the grand totals (summed over blocks in index order).
+// Publishes the N partials of (virtual) block vb of nvb and returns true in every thread of
+// the block that publishes last, whose thread-0 `v` then holds the grand totals (summed over
+// blocks in index order, so the result does not depend on which block comes last).
 template <int N>
-__device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsigned int* counter, double* scratch) {
+__device__ __forceinline__ bool grid_sum_v(double (&v)[N], double* partials, unsigned int* counter, double* scratch,
+                                           int vb, int nvb) {
   __shared__ bool s_last;
   block_sum<N>(v, scratch);
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) partials[blockIdx.x * N + k] = v[k];
+    for (int k = 0; k < N; ++k) partials[vb * N + k] = v[k];
     __threadfence();
     const unsigned t = atomicAdd(counter, 1u);
-    s_last = (t == gridDim.x - 1);
+    s_last = (t == (unsigned)nvb - 1u);
   }
   __syncthreads();
   if (!s_last) return false;
@@ -52,16 +54,21 @@ __device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsig
   double acc[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+  for (int b = threadIdx.x; b < nvb; b += blockDim.x)
 #pragma unroll
     for (int k = 0; k < N; ++k) acc[k] += __ldcg(partials + b * N + k);
   block_sum<N>(acc, scratch);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < N; ++k) v[k] = acc[k];
-    *counter = 0u;  // ready for the next launch (stream order makes this safe)
+    *counter = 0u;  // ready for the next use (stream order or a grid barrier makes this safe)
   }
   return true;
+}
+
+template <int N>
+__device__ __forceinline__ bool grid_sum(double (&v)[N], double* partials, unsigned int* counter, double* scratch) {
+  return grid_sum_v<N>(v, partials, counter, scratch, blockIdx.x, gridDim.x);
 }
 
 }  // namespace pfem

@@ -114,6 +114,11 @@ struct Request {
   double ref = 1.0, t_ls = 1.0;
   int newton = 0, inner_iters = 0, repl = 0, backtracks = 0, ls_tries = 0;
   double init_rel = -1.0, last_rel = 0.0;
+  // FP64 replacements of the current PCG solve: a true residual that improves by less than
+  // 2x twice in a row ends a Newton inner solve as stagnated (the FP32 operator's limit)
+  bool replaced = false;
+  double prev_true = -1.0;
+  int stalls = 0;
   // result
   std::vector<double> result;
   pfem_solve_info info{};
@@ -156,7 +161,7 @@ struct pfem_server_s {
   StateSlot* d_slots = nullptr;
   StateSlot* h_slots = nullptr;
   size_t cap_reqs = 0, cap_btile = 0, cap_ublk = 0;
-  int n_apply = 0, n_update = 0, max_local = 1, slot_cap = 4;
+  int n_apply = 0, n_update = 0, max_local = 1, slot_cap = 4, step_cap = 1;
   std::vector<int> active_index;   // position of each active request in the tables
 };
 
@@ -238,10 +243,14 @@ pfem_status enq_pcg_start(Request* R, bool newton, double tol, const double* ref
     if ((st = launch_element_op(R->mesh->plan, OP_TANGENT, PFEM_F64, PFEM_F64, a, s))) return st;
     if ((st = vk_axpy(R->n, 1.0, R->rn, R->res, s))) return st;
   }
+  R->replaced = true;
+  R->prev_true = -1.0;
+  R->stalls = 0;
   return vk_replace(R->n, R->res, R->r, R->dinv, R->st, 1, R->mesh->red_partials, R->mesh->red_counter, s);
 }
 
 pfem_status enq_replacement(Request* R, bool newton, cudaStream_t s) {
+  R->replaced = true;
   pfem_status st;
   if (!newton) {
     if ((st = enq_residual64(R, R->x, R->res, 1.0, s))) return st;
@@ -399,8 +408,22 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
       R->phase = PH_NT_INNER;
       break;
     }
-    case PH_NT_INNER:
-      if (ps.done == PCG_CONVERGED || ps.done == PCG_MAXITER) {
+    case PH_NT_INNER: {
+      bool stagnated = false;
+      if (R->replaced) {
+        R->replaced = false;
+        R->stalls = (R->prev_true > 0.0 && !(ps.rel_true < 0.5 * R->prev_true)) ? R->stalls + 1 : 0;
+        R->prev_true = ps.rel_true;
+        stagnated = R->stalls >= 2 && ps.done == 0;
+      }
+      if (stagnated) {  // take the solve out of the shared steps before the line search
+        static const int kStagnated = PCG_STAGNATED;
+        if (cudaMemcpyAsync(&R->st->done, &kStagnated, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+          st = PFEM_ERR_CUDA;
+          break;
+        }
+      }
+      if (ps.done == PCG_CONVERGED || ps.done == PCG_MAXITER || stagnated) {
         R->inner_iters += ps.iter;
         R->repl += ps.replacements;
         R->t_ls = 1.0;
@@ -412,6 +435,7 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
         st = enq_replacement(R, true, s);
       }
       break;
+    }
     case PH_NT_LS:
       if (sl.inverted == 0) {
         cudaMemcpyAsync(R->u, R->tmp, (size_t)R->n * 8, cudaMemcpyDeviceToDevice, s);
@@ -440,7 +464,7 @@ pfem_status rebuild_tables(pfem_server_s* S) {
   std::vector<PcgState*> stp((size_t)na);
   std::vector<double*> auxp((size_t)na);
   std::vector<int32_t*> invp((size_t)na);
-  int max_local = 1, slot_cap = 4;
+  int max_local = 1, slot_cap = 4, step_cap = 1;
   for (int i = 0; i < na; ++i) {
     Request* R = S->active[(size_t)i];
     ReqDev& d = reqs[(size_t)i];
@@ -464,6 +488,7 @@ pfem_status rebuild_tables(pfem_server_s* S) {
     for (int k = 0; k < R->nublk; ++k) ublk.push_back(i);
     max_local = std::max(max_local, d.plan.max_local);
     slot_cap = std::max(slot_cap, d.plan.slot_cap);
+    step_cap = std::max(step_cap, d.plan.step_cap);
     stp[(size_t)i] = R->st;
     auxp[(size_t)i] = R->aux;
     invp[(size_t)i] = R->mesh->plan.inverted;
@@ -505,6 +530,7 @@ pfem_status rebuild_tables(pfem_server_s* S) {
   S->n_update = (int)ublk.size();
   S->max_local = max_local;
   S->slot_cap = slot_cap;
+  S->step_cap = step_cap;
   S->dirty = false;
   return PFEM_OK;
 }
@@ -590,7 +616,7 @@ void worker_loop(pfem_server_s* S) {
     }
     // ---- a chunk of shared steps, then one read-back of every solve's scalars
     for (int k = 0; k < chunk; ++k)
-      launch_serve_step(S->d_reqs, S->d_btile, S->n_apply, S->d_ublk, S->n_update, S->max_local, S->slot_cap,
+      launch_serve_step(S->d_reqs, S->d_btile, S->n_apply, S->d_ublk, S->n_update, S->max_local, S->slot_cap, S->step_cap,
                         S->stream);
     const int na = (int)S->active.size();
     gather_states_kernel<<<(na + 127) / 128, 128, 0, S->stream>>>(S->d_stp, S->d_auxp, S->d_invp, na, S->d_slots);

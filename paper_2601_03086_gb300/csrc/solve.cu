@@ -36,7 +36,6 @@ struct SolverWS {
   double* tile_part = nullptr;       // per-tile p . A p partials of the fused apply
   unsigned int* ticket = nullptr;    // last-tile ticket of the fused apply
   GridBar* bar = nullptr;            // grid barrier of the persistent kernel
-  double* red_part = nullptr;        // kReduceBlocks x 2 partials of the persistent kernel
   PcgState* st = nullptr;    // device
   PcgState* hst = nullptr;   // pinned host mirror
   double* dnorm = nullptr;   // device scalar
@@ -84,7 +83,7 @@ static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
   w->n = m->n_dofs;
   const size_t vb = ((size_t)w->n * sizeof(double) + 255) & ~size_t(255);
   const size_t tb = ((size_t)std::max(m->plan.n_tiles, 1) * sizeof(double) + 255) & ~size_t(255);
-  w->bytes = 10 * vb + tb + 768 + 4864;
+  w->bytes = 10 * vb + tb + 768;
   cudaError_t e = cudaMalloc(&w->block, w->bytes);
   if (e != cudaSuccess) {
     delete w;
@@ -98,7 +97,6 @@ static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
   w->dnorm = reinterpret_cast<double*>(b + 10 * vb + tb + 256);
   w->ticket = reinterpret_cast<unsigned int*>(b + 10 * vb + tb + 512);
   w->bar = reinterpret_cast<GridBar*>(b + 10 * vb + tb + 640);
-  w->red_part = reinterpret_cast<double*>(b + 10 * vb + tb + 768);
   e = cudaMemset(w->ticket, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMallocHost(&w->hst, sizeof(PcgState));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking);
@@ -200,52 +198,74 @@ static pfem_status read_state(pfem_mesh_t m, SolverWS* w) {
 }
 
 // Runs PCG from the current x (dinv, ref, tol, max_iter already set in the device state).
+//
+// Stagnation: an FP32 operator limits how far the true residual can fall (its rounding is a
+// fixed fraction of ||A|| ||x||). When two consecutive FP64 replacements improve the true
+// residual by less than 2x, a Newton inner solve stops with PCG_STAGNATED (its direction is
+// as accurate as the arithmetic allows, and Newton checks progress in FP64 anyway); a linear
+// solve continues with the FP64 element operator.
 static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u, bool newton_inner) {
+  static const int kStagnated = PCG_STAGNATED;
   cudaStream_t s = m->stream;
   pfem_status st;
+  const int ui = use_u ? 1 : 0;
   // both direction buffers start at zero (the first direction is p = dinv r with beta = 0)
   PFEM_CUDA(cudaMemsetAsync(w->p, 0, (size_t)w->n * sizeof(double), s));
   PFEM_CUDA(cudaMemsetAsync(w->p2, 0, (size_t)w->n * sizeof(double), s));
   if ((st = true_residual(m, w, newton_inner, s))) return st;
   if ((st = vk_replace(w->n, w->res, w->r, w->dinv, w->st, 1, m->red_partials, m->red_counter, s))) return st;
-  cudaGraphExec_t* ex = &w->exec[ct == PFEM_F64][use_u ? 1 : 0];
-  bool use_persist = g_solver_mode == 0 && ct != PFEM_F64 && !w->persist_failed[use_u ? 1 : 0];
-  const bool use_graph = (g_solver_mode == 2 || (g_solver_mode == 0 && !use_persist)) && !w->graph_failed;
-  if (use_graph && !*ex) {
-    if (build_graph(m, w, ct, use_u, ex) != PFEM_OK) {
-      w->graph_failed = true;
-      *ex = nullptr;
-    }
-  }
+  bool replaced = true;  // the start is an FP64 true residual too
+  double prev_true = -1.0;
+  int stalls = 0;
   int pending_iter0 = -1;  // iteration count before the last graph launch
-  const int64_t body = w->body_kernels[ct == PFEM_F64][use_u ? 1 : 0];
+  int64_t pending_body = 0;
   for (;;) {
     if ((st = read_state(m, w))) return st;
     if (pending_iter0 >= 0) {  // a graph replay ran (iterations x body) + the pre-node
-      g_kernel_launches += (int64_t)(w->hst->iter - pending_iter0) * body + 1;
+      g_kernel_launches += (int64_t)(w->hst->iter - pending_iter0) * pending_body + 1;
       pending_iter0 = -1;
+    }
+    if (replaced) {
+      replaced = false;
+      const double rt = w->hst->rel_true;
+      stalls = (prev_true > 0.0 && !(rt < 0.5 * prev_true)) ? stalls + 1 : 0;
+      prev_true = rt;
+      if (stalls >= 2 && w->hst->done == 0) {
+        if (newton_inner) {
+          PFEM_CUDA(cudaMemcpyAsync(&w->st->done, &kStagnated, sizeof(int), cudaMemcpyHostToDevice, s));
+          PFEM_CUDA(cudaStreamSynchronize(s));
+          w->hst->done = PCG_STAGNATED;
+          break;
+        }
+        if (ct != PFEM_F64) {
+          ct = PFEM_F64;
+          stalls = 0;
+        }
+      }
     }
     if (w->hst->done != 0) break;
     if (w->hst->repl != 0) {
       if ((st = true_residual(m, w, newton_inner, s))) return st;
       if ((st = vk_replace(w->n, w->res, w->r, w->dinv, w->st, 0, m->red_partials, m->red_counter, s))) return st;
+      replaced = true;
       continue;
     }
-    if (use_persist) {
+    if (g_solver_mode == 0 && ct != PFEM_F64 && !w->persist_failed[ui]) {
       PersistArgs pa{use_u ? w->u : nullptr, w->x, w->r, w->dinv, {w->p, w->p2}, w->q, w->st, w->tile_part,
-                     w->red_part, w->bar, w->n};
+                     w->ticket, m->red_partials, m->red_counter, w->bar, w->n};
       st = launch_pcg_persistent(m->plan, ct, pa, s);
       if (st == PFEM_OK) continue;
       if (st != PFEM_ERR_UNSUPPORTED) return st;
-      w->persist_failed[use_u ? 1 : 0] = true;  // falls back to the graph (or plain) loop
-      use_persist = false;
-      if (g_solver_mode == 0 && !w->graph_failed && !*ex && build_graph(m, w, ct, use_u, ex) != PFEM_OK) {
-        w->graph_failed = true;
-        *ex = nullptr;
-      }
+      w->persist_failed[ui] = true;  // falls back to the graph (or plain) loop
     }
-    if (!w->graph_failed && *ex && g_solver_mode != 1) {
+    cudaGraphExec_t* ex = &w->exec[ct == PFEM_F64][ui];
+    if (g_solver_mode != 1 && !w->graph_failed && !*ex && build_graph(m, w, ct, use_u, ex) != PFEM_OK) {
+      w->graph_failed = true;
+      *ex = nullptr;
+    }
+    if (g_solver_mode != 1 && !w->graph_failed && *ex) {
       pending_iter0 = w->hst->iter;
+      pending_body = w->body_kernels[ct == PFEM_F64][ui];
       PFEM_CUDA(cudaGraphLaunch(*ex, s));
     } else {
       if ((st = pcg_body(m, w, ct, use_u, s, cudaGraphConditionalHandle(), 0))) return st;
@@ -294,6 +314,7 @@ static pfem_status status_of(int done) {
     case PCG_CONVERGED: return PFEM_OK;
     case PCG_MAXITER: return PFEM_ERR_NOT_CONVERGED;
     case PCG_NONFINITE: return PFEM_ERR_NONFINITE;
+    case PCG_STAGNATED: set_error("PCG stagnated above the tolerance with the FP64 operator"); return PFEM_ERR_NOT_CONVERGED;
     case PCG_BARRIER_TIMEOUT: set_error("a grid barrier of the persistent PCG kernel timed out"); return PFEM_ERR_TIMEOUT;
     default: return PFEM_ERR_NOT_CONVERGED;
   }
@@ -412,7 +433,7 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
       if ((st = read_state(m, w))) break;
       total_inner += w->hst->iter;
       n_repl += w->hst->replacements;
-      if (w->hst->done != PCG_CONVERGED && w->hst->done != PCG_MAXITER) {
+      if (w->hst->done != PCG_CONVERGED && w->hst->done != PCG_MAXITER && w->hst->done != PCG_STAGNATED) {
         result = status_of(w->hst->done);
         set_error("inner PCG failed with state %d", w->hst->done);
         break;

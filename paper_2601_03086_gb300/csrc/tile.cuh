@@ -19,6 +19,7 @@
 #pragma once
 
 #include <cuda/atomic>
+#include <type_traits>
 
 #include "element.cuh"
 #include "pcg_state.cuh"
@@ -31,15 +32,23 @@ enum : int { OUT_RES = 0, OUT_TAN = 1, OUT_DIAG = 2 };
 
 template <typename CT>
 struct SmemLayout {
-  size_t slot, x, u, v, off, info, red, total;
+  size_t slot, x, u, v, off, info, red, fb, head, smat, scode, total;
 };
 
-// Shared memory: 4-wide (x, y, z, pad) records for slots and staged node data.
+// Shared memory: 4-wide (x, y, z, pad) records for slots and staged node data; the tile's
+// fan heads, step materials and step codes (step_cap >= fans and steps of any tile).
 template <typename CT>
-__host__ __device__ inline SmemLayout<CT> smem_layout(int max_local, int slot_cap, bool need_u, bool need_v) {
+__host__ __device__ inline SmemLayout<CT> smem_layout(int max_local, int slot_cap, int step_cap, bool need_u,
+                                                      bool need_v) {
   SmemLayout<CT> L;
   size_t o = 0;
   auto al = [](size_t x) { return (x + 31) & ~size_t(31); };
+  L.head = o;
+  o = al(o + (size_t)step_cap * sizeof(ushort4));
+  L.smat = o;
+  o = al(o + (size_t)step_cap * 2 * sizeof(CT));
+  L.scode = o;
+  o = al(o + (size_t)step_cap * sizeof(uint16_t));
   L.slot = o;
   o = al(o + (size_t)slot_cap * 4 * sizeof(CT));
   L.x = o;
@@ -54,6 +63,8 @@ __host__ __device__ inline SmemLayout<CT> smem_layout(int max_local, int slot_ca
   o = al(o + (size_t)max_local * sizeof(int));
   L.red = o;
   o = al(o + 32 * sizeof(double));
+  L.fb = o;
+  o = al(o + kMaxFan * sizeof(int));
   L.total = o;
   return L;
 }
@@ -132,107 +143,211 @@ __device__ __forceinline__ double corner_dot(const CT (&w)[DIM + 1][3], const CT
   return (double)s;
 }
 
-// One element pass for output OUT (or energy only when OUT < 0). PAP: accumulate v . A_e v
-// into e_acc (tangent pass of the PCG-fused apply).
+// One fan pass for output OUT (or energy only when OUT < 0): thread f walks the ring of fan
+// f once (see pfem_internal.h), evaluates its simplices in ring order and writes one slot per
+// (fan, node). PAP: accumulate v . (A v) restricted to the fan's nodes into e_acc (tangent
+// pass of the PCG-fused apply; summed over fans this is v . A v).
 template <int DIM, int KIND, int OUT, bool ENERGY, bool COUNT, typename CT, bool PAP = false>
-__device__ __forceinline__ void element_pass(const DevPlan& P, unsigned char* smem, const SmemLayout<CT>& L, int ebeg,
-                                             int ne, double& e_acc, int& n_inv) {
+__device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<CT>& L, int nf, double& e_acc,
+                                         int& n_inv) {
   constexpr int NV = DIM + 1;
+  constexpr int HS = DIM - 1;  // hinge nodes
+  constexpr bool NEED_GU = ENERGY || OUT == OUT_RES || (KIND == K_NH && (OUT == OUT_TAN || OUT == OUT_DIAG));
+  constexpr bool NEED_GV = OUT == OUT_TAN;
   const CT* sx = reinterpret_cast<const CT*>(smem + L.x);
   const CT* su = reinterpret_cast<const CT*>(smem + L.u);
   const CT* sv = reinterpret_cast<const CT*>(smem + L.v);
   const int* soff = reinterpret_cast<const int*>(smem + L.off);
+  const int* scnt = reinterpret_cast<const int*>(smem + L.fb);  // fans with more than i simplices
+  const ushort4* shead = reinterpret_cast<const ushort4*>(smem + L.head);
+  using M2 = typename std::conditional<sizeof(CT) == 4, float2, double2>::type;
+  const M2* smat = reinterpret_cast<const M2*>(smem + L.smat);
+  const uint16_t* scode = reinterpret_cast<const uint16_t*>(smem + L.scode);
   CT* slot = reinterpret_cast<CT*>(smem + L.slot);
-  for (int e = threadIdx.x; e < ne; e += blockDim.x) {
-    const ushort4 code = P.ecode[ebeg + e];
-    const unsigned short cs[4] = {code.x, code.y, code.z, code.w};
-    CT mu, lam;
-    if constexpr (sizeof(CT) == 4) {
-      const float2 m = P.emat_f[ebeg + e];
-      mu = m.x;
-      lam = m.y;
-    } else {
-      const double2 m = P.emat_d[ebeg + e];
-      mu = m.x;
-      lam = m.y;
-    }
-    int loc[NV];
-    CT X[NV][4];
+  auto put = [&](unsigned code, const CT (&acc)[DIM]) {
+    const int sl = soff[code & 1023u] + (int)(code >> 10);
+    st4(slot + 4 * sl, acc[0], acc[1], DIM == 3 ? acc[DIM - 1] : CT(0), CT(0));
+  };
+  auto dot3 = [](const CT (&a)[3], const CT (&b)[DIM]) {
+    CT t = a[0] * b[0];
 #pragma unroll
-    for (int a = 0; a < NV; ++a) {
-      loc[a] = cs[a] & 1023;
-      ld4(sx + 4 * loc[a], X[a]);
-    }
-    ElemGeo<DIM, CT> G;
-    geometry<DIM, CT>(X, G);
-    constexpr bool NEED_GU = ENERGY || OUT == OUT_RES || (KIND == K_NH && (OUT == OUT_TAN || OUT == OUT_DIAG));
-    auto load_w = [&](const CT* base, CT (&w)[NV][3]) {
+    for (int i = 1; i < DIM; ++i) t = fma(a[i], b[i], t);
+    return (double)t;
+  };
+  for (int f = threadIdx.x; f < nf; f += blockDim.x) {
+    const ushort4 hd = shead[f];
+    const int k = hd.w;
+    CT x0[4], u0[4] = {}, v0[4] = {};
+    ld4(sx + 4 * (hd.x & 1023), x0);
+    if constexpr (NEED_GU) ld4(su + 4 * (hd.x & 1023), u0);
+    if constexpr (NEED_GV) ld4(sv + 4 * (hd.x & 1023), v0);
+    CT H[3] = {CT(0), CT(0), CT(0)}, duH[3] = {CT(0), CT(0), CT(0)}, dvH[3] = {CT(0), CT(0), CT(0)};
+    CT v1[3] = {CT(0), CT(0), CT(0)};
+    if constexpr (DIM == 3) {
+      CT t[4];
+      ld4(sx + 4 * (hd.y & 1023), t);
 #pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        CT t[4];
-        ld4(base + 4 * loc[a], t);
-        w[a][0] = t[0], w[a][1] = t[1], w[a][2] = t[2];
+      for (int i = 0; i < 3; ++i) H[i] = t[i] - x0[i];
+      if constexpr (NEED_GU) {
+        ld4(su + 4 * (hd.y & 1023), t);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) duH[i] = t[i] - u0[i];
+      }
+      if constexpr (NEED_GV) {
+        ld4(sv + 4 * (hd.y & 1023), t);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          dvH[i] = t[i] - v0[i];
+          v1[i] = t[i];
+        }
+      }
+    }
+    // ring node state: edge from h_0, H x edge, field differences from h_0, raw v (PAP)
+    auto load_ring = [&](unsigned code, CT (&E)[3], CT (&Q)[3], CT (&du)[3], CT (&dv)[3], CT (&vr)[3]) {
+      const int l = (int)(code & 1023u);
+      CT t[4];
+      ld4(sx + 4 * l, t);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) E[i] = t[i] - x0[i];
+      if constexpr (DIM == 3) {
+        Q[0] = H[1] * E[2] - H[2] * E[1];
+        Q[1] = H[2] * E[0] - H[0] * E[2];
+        Q[2] = H[0] * E[1] - H[1] * E[0];
+      }
+      if constexpr (NEED_GU) {
+        ld4(su + 4 * l, t);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) du[i] = t[i] - u0[i];
+      }
+      if constexpr (NEED_GV) {
+        ld4(sv + 4 * l, t);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          dv[i] = t[i] - v0[i];
+          vr[i] = t[i];
+        }
       }
     };
-    CT out[NV][DIM];
-    if constexpr (KIND == K_LIN) {
-      // linear law: everything from the unscaled gradient G' (grad = G'/det)
-      if constexpr (NEED_GU) {
-        CT w[NV][3], Gp[DIM][DIM];
-        load_w(su, w);
-        grad_prime<DIM, CT>(G, w, Gp);
-        if constexpr (ENERGY) e_acc += (double)linear_energy<DIM, CT>(G, Gp, mu, lam);
-        if constexpr (OUT == OUT_RES) linear_force<DIM, CT>(G, Gp, mu, lam, out);
-      }
-      if constexpr (OUT == OUT_TAN) {
-        CT w[NV][3], Gp[DIM][DIM];
-        load_w(sv, w);
-        grad_prime<DIM, CT>(G, w, Gp);
-        linear_force<DIM, CT>(G, Gp, mu, lam, out);
-        if constexpr (PAP) e_acc += corner_dot<DIM, CT>(w, out);
-      } else if constexpr (OUT == OUT_DIAG) {
-        nh_diag<DIM, CT>(G, static_cast<const NHState<DIM, CT>*>(nullptr), mu, lam, out);
-      }
-    } else {
-      CT Gu[DIM][DIM];
-      {
-        CT w[NV][3];
-        load_w(su, w);
-        grad_of<DIM, CT>(G, w, Gu);
-      }
-      NHState<DIM, CT> s;
-      nh_state<DIM, CT>(Gu, s);
-      if (COUNT && !(s.J > CT(0))) ++n_inv;
-      if constexpr (ENERGY) {
-        const CT psi = s.J > CT(0) ? nh_psi<DIM, CT>(s, mu, lam) : CT(INFINITY);
-        e_acc += (double)(fabs(G.det) * CT(1.0 / Factorial<DIM>::value) * psi);
-      }
-      if constexpr (OUT == OUT_RES || OUT == OUT_TAN) {
-        CT T[DIM][DIM];
-        CT w[NV][3];
-        if constexpr (OUT == OUT_RES) {
-          nh_pk1<DIM, CT>(s, mu, lam, T);
-        } else {
-          CT Gv[DIM][DIM];
-          load_w(sv, w);
-          grad_of<DIM, CT>(G, w, Gv);
-          nh_dpk1<DIM, CT>(s, mu, lam, Gv, T);
+    CT acc0[DIM], acc1[DIM], accc[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) acc0[i] = acc1[i] = accc[i] = CT(0);
+    unsigned cc = hd.z;
+    CT Ec[3], Qc[3] = {CT(0), CT(0), CT(0)}, duc[3] = {CT(0), CT(0), CT(0)}, dvc[3] = {CT(0), CT(0), CT(0)},
+              vc[3] = {CT(0), CT(0), CT(0)};
+    load_ring(cc, Ec, Qc, duc, dvc, vc);
+    int s = f;  // step record of the tile (step-major: step i of fan f at sum_{j<i} cnt_j + f)
+    for (int i = 0; i < k; ++i) {
+      const unsigned cn = scode[s];
+      const M2 m = smat[s];
+      const CT mu = m.x, lam = m.y;
+      s += scnt[i];
+      CT En[3], Qn[3] = {CT(0), CT(0), CT(0)}, dun[3] = {CT(0), CT(0), CT(0)}, dvn[3] = {CT(0), CT(0), CT(0)},
+                vn[3] = {CT(0), CT(0), CT(0)};
+      load_ring(cn, En, Qn, dun, dvn, vn);
+      ElemGeo<DIM, CT> G;
+      fan_geometry<DIM, CT>(H, Ec, En, Qc, Qn, G);
+      // corner differences from h_0 of the simplex's fields
+      auto diffs = [&](const CT (&dh)[3], const CT (&dci)[3], const CT (&dcn)[3], CT (&dw)[DIM][3]) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          if constexpr (DIM == 3) {
+            dw[0][j] = dh[j];
+            dw[1][j] = dci[j];
+            dw[2][j] = dcn[j];
+          } else {
+            dw[0][j] = dci[j];
+            dw[1][j] = dcn[j];
+          }
         }
+      };
+      CT out[NV][DIM];
+      if constexpr (KIND == K_LIN) {
+        if constexpr (NEED_GU) {
+          CT dw[DIM][3], Gp[DIM][DIM];
+          diffs(duH, duc, dun, dw);
+          grad_prime_d<DIM, CT>(G, dw, Gp);
+          if constexpr (ENERGY) e_acc += (double)linear_energy<DIM, CT>(G, Gp, mu, lam);
+          if constexpr (OUT == OUT_RES) linear_force<DIM, CT>(G, Gp, mu, lam, out);
+        }
+        if constexpr (OUT == OUT_TAN) {
+          CT dw[DIM][3], Gp[DIM][DIM];
+          diffs(dvH, dvc, dvn, dw);
+          grad_prime_d<DIM, CT>(G, dw, Gp);
+          linear_force<DIM, CT>(G, Gp, mu, lam, out);
+        } else if constexpr (OUT == OUT_DIAG) {
+          nh_diag<DIM, CT>(G, static_cast<const NHState<DIM, CT>*>(nullptr), mu, lam, out);
+        }
+      } else {
+        CT Gu[DIM][DIM];
+        {
+          CT dw[DIM][3];
+          diffs(duH, duc, dun, dw);
+          grad_prime_d<DIM, CT>(G, dw, Gu);
 #pragma unroll
-        for (int i = 0; i < DIM; ++i)
+          for (int a = 0; a < DIM; ++a)
 #pragma unroll
-          for (int j = 0; j < DIM; ++j) T[i][j] *= G.kappa;  // V T dN_a = kappa T c_a
-        contract_c<DIM, CT>(G, T, out);
-        if constexpr (OUT == OUT_TAN && PAP) e_acc += corner_dot<DIM, CT>(w, out);
-      } else if constexpr (OUT == OUT_DIAG) {
-        nh_diag<DIM, CT>(G, &s, mu, lam, out);
+            for (int b = 0; b < DIM; ++b) Gu[a][b] *= G.rdet;
+        }
+        NHState<DIM, CT> st;
+        nh_state<DIM, CT>(Gu, st);
+        if (COUNT && !(st.J > CT(0))) ++n_inv;
+        if constexpr (ENERGY) {
+          const CT psi = st.J > CT(0) ? nh_psi<DIM, CT>(st, mu, lam) : CT(INFINITY);
+          e_acc += (double)(fabs(G.det) * CT(1.0 / Factorial<DIM>::value) * psi);
+        }
+        if constexpr (OUT == OUT_RES || OUT == OUT_TAN) {
+          CT T[DIM][DIM];
+          if constexpr (OUT == OUT_RES) {
+            nh_pk1<DIM, CT>(st, mu, lam, T);
+          } else {
+            CT dw[DIM][3], Gv[DIM][DIM];
+            diffs(dvH, dvc, dvn, dw);
+            grad_prime_d<DIM, CT>(G, dw, Gv);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+#pragma unroll
+              for (int b = 0; b < DIM; ++b) Gv[a][b] *= G.rdet;
+            nh_dpk1<DIM, CT>(st, mu, lam, Gv, T);
+          }
+#pragma unroll
+          for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) T[a][b] *= G.kappa;  // V T dN_a = kappa T c_a
+          contract_c<DIM, CT>(G, T, out);
+        } else if constexpr (OUT == OUT_DIAG) {
+          nh_diag<DIM, CT>(G, &st, mu, lam, out);
+        }
+      }
+      if constexpr (OUT >= 0) {
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) {
+          acc0[j] += out[0][j];
+          if constexpr (DIM == 3) acc1[j] += out[1][j];
+          accc[j] += out[HS][j];
+        }
+        put(cc, accc);  // ring node i is complete: it touches simplices i - 1 and i only
+        if constexpr (PAP) e_acc += dot3(vc, accc);
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) accc[j] = out[HS + 1][j];
+      }
+      cc = cn;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Ec[j] = En[j];
+        Qc[j] = Qn[j];
+        duc[j] = dun[j];
+        dvc[j] = dvn[j];
+        vc[j] = vn[j];
       }
     }
     if constexpr (OUT >= 0) {
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        const int sl = soff[loc[a]] + (cs[a] >> 10);
-        st4(slot + 4 * sl, out[a][0], out[a][1], DIM == 3 ? out[a][DIM - 1] : CT(0), CT(0));
+      put(cc, accc);
+      put(hd.x, acc0);
+      if constexpr (DIM == 3) put(hd.y, acc1);
+      if constexpr (PAP) {
+        CT v0c[3] = {v0[0], v0[1], v0[2]};
+        e_acc += dot3(vc, accc) + dot3(v0c, acc0);
+        if constexpr (DIM == 3) e_acc += dot3(v1, acc1);
       }
     }
   }
@@ -261,14 +376,20 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
       final_write<DIM, OUT, VT, CT, PCG>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, acc);
       continue;
     }
-    // halo node: publish this tile's partial, the tile completing the set finishes the node
-    const int pi = pbeg + l - ncomp;
-    st4(part + 4 * (size_t)pi, acc[0], acc[1], acc[2], CT(0));
-    const int h = P.partial_halo[pi];
+    // halo node: publish this tile's partial
+    st4(part + 4 * (size_t)(pbeg + l - ncomp), acc[0], acc[1], acc[2], CT(0));
+  }
+  // Release once per tile: every partial of this tile is visible device-wide before any of
+  // its tickets; the tile whose ticket completes a halo node's set (acquire fence after the
+  // ticket) sums that node's partials in ascending tile order and writes the output.
+  __syncthreads();
+  if (threadIdx.x == 0) __threadfence();
+  __syncthreads();
+  for (int l = ncomp + threadIdx.x; l < nl; l += blockDim.x) {
+    const int h = P.partial_halo[pbeg + l - ncomp];
     const int pb = P.halo_ptr[h], pe = P.halo_ptr[h + 1];
-    // release: this partial is visible before the ticket; acquire: the last tile sees all
-    cuda::atomic_ref<int32_t, cuda::thread_scope_device> ticket(count[h]);
-    if (ticket.fetch_add(1, cuda::memory_order_acq_rel) == pe - pb - 1) {
+    if (atomicAdd(count + h, 1) == pe - pb - 1) {
+      __threadfence();
       CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
       for (int k = pb; k < pe; ++k) {
         CT t[4];
@@ -296,14 +417,13 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
 template <int DIM, int KIND, int OPS, typename VT, typename CT>
 __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, int t, unsigned char* smem,
                                              const SmemLayout<CT>& lay) {
-  constexpr int NV = DIM + 1;
   constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
   const SmemLayout<CT>& L = lay;
   const int4 ta = P.tile_a[t];
   const int4 tb = P.tile_b[t];
-  const int ebeg = ta.x, ne = ta.y, lbeg = ta.z, nl = ta.w;
-  const int ncomp = tb.x, pbeg = tb.y;
+  const int fbeg = ta.x, nf = ta.y, lbeg = ta.z, nl = ta.w;
+  const int ncomp = tb.x, pbeg = tb.y, sbeg = tb.z, ns = tb.w;
   constexpr bool PCG = (OPS & OP_PCG) != 0;
   const double* p_old = nullptr;
   double* p_new = nullptr;
@@ -371,7 +491,23 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
         st4(sv + 4 * l, w[0], w[1], w[2], CT(0));
       }
     }
-    if (threadIdx.x == 0) soff[nl] = ne * NV;
+    if (threadIdx.x == 0) soff[nl] = nf * DIM + ns;  // slots: DIM + k per fan
+    {  // the tile's fan heads and step records (coalesced; read from shared memory by the fans)
+      ushort4* shead = reinterpret_cast<ushort4*>(smem + L.head);
+      uint16_t* scode = reinterpret_cast<uint16_t*>(smem + L.scode);
+      for (int j = threadIdx.x; j < nf; j += blockDim.x) shead[j] = P.fan_head[fbeg + j];
+      for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+        scode[j] = P.step_code[sbeg + j];
+        if constexpr (sizeof(CT) == 4) reinterpret_cast<float2*>(smem + L.smat)[j] = P.step_mat_f[sbeg + j];
+        else reinterpret_cast<double2*>(smem + L.smat)[j] = P.step_mat_d[sbeg + j];
+      }
+    }
+    if (threadIdx.x < kMaxFan) {  // fan counts per step (8 x uint16 in one uint4)
+      const uint4 c = P.tile_cnt[t];
+      const unsigned q = threadIdx.x >> 1;
+      const unsigned word = q == 0 ? c.x : (q == 1 ? c.y : (q == 2 ? c.z : c.w));
+      reinterpret_cast<int*>(smem + L.fb)[threadIdx.x] = (int)((word >> (16 * (threadIdx.x & 1))) & 0xffffu);
+    }
   }
   __syncthreads();
 
@@ -379,23 +515,22 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
   int n_inv = 0;
   int region = 0;
   if constexpr ((OPS & OP_RESIDUAL) != 0) {
-    element_pass<DIM, KIND, OUT_RES, (OPS & OP_ENERGY) != 0, true, CT>(P, smem, L, ebeg, ne, e_acc, n_inv);
+    fan_pass<DIM, KIND, OUT_RES, (OPS & OP_ENERGY) != 0, true, CT>(smem, L, nf, e_acc, n_inv);
     __syncthreads();
     node_pass<DIM, OUT_RES, VT, CT>(P, A, smem, L, nl, ncomp, pbeg, region++);
     __syncthreads();
   } else if constexpr ((OPS & OP_ENERGY) != 0) {
-    element_pass<DIM, KIND, -1, true, true, CT>(P, smem, L, ebeg, ne, e_acc, n_inv);
+    fan_pass<DIM, KIND, -1, true, true, CT>(smem, L, nf, e_acc, n_inv);
   }
   if constexpr ((OPS & OP_TANGENT) != 0) {
-    element_pass<DIM, KIND, OUT_TAN, false, (OPS & (OP_RESIDUAL | OP_ENERGY)) == 0, CT, PCG>(P, smem, L, ebeg, ne,
-                                                                                          e_acc, n_inv);
+    fan_pass<DIM, KIND, OUT_TAN, false, (OPS & (OP_RESIDUAL | OP_ENERGY)) == 0, CT, PCG>(smem, L, nf, e_acc, n_inv);
     __syncthreads();
     node_pass<DIM, OUT_TAN, VT, CT, PCG>(P, A, smem, L, nl, ncomp, pbeg, region++, p_old, p_new, beta);
     __syncthreads();
   }
   if constexpr ((OPS & OP_DIAG) != 0) {
-    element_pass<DIM, KIND, OUT_DIAG, false, (OPS & (OP_RESIDUAL | OP_ENERGY | OP_TANGENT)) == 0, CT>(
-        P, smem, L, ebeg, ne, e_acc, n_inv);
+    fan_pass<DIM, KIND, OUT_DIAG, false, (OPS & (OP_RESIDUAL | OP_ENERGY | OP_TANGENT)) == 0, CT>(
+        smem, L, nf, e_acc, n_inv);
     __syncthreads();
     node_pass<DIM, OUT_DIAG, VT, CT>(P, A, smem, L, nl, ncomp, pbeg, region++);
   }
@@ -418,7 +553,7 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
       else P.tile_energy[t] = s;
     }
   }
-  if constexpr (PCG && !PERSIST) {
+  if constexpr (PCG) {
     // the last tile to finish sums the tile partials in tile order: alpha = rho / (p . A p)
     __shared__ bool s_last;
     if (threadIdx.x == 0) {
@@ -445,7 +580,7 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
           st->alpha = 0.0;
           st->done = isfinite(pap) ? PCG_BREAKDOWN : PCG_NONFINITE;
         } else {
-          st->alpha = st->rho / pap;
+          st->alpha = __ldcg(&st->rho) / pap;
         }
         *A.pcg.ticket = 0u;
       }
