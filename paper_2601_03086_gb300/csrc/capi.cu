@@ -81,11 +81,9 @@ size_t mesh_arena_bytes(const HostPlan& hp) {
   take(hp.step_code.size() * 2);
   take(hp.step_mat_f.size() * 4);
   take(hp.step_mat_d.size() * 8);
-  take(hp.halo_info.size() * 4);
-  take(hp.halo_ptr.size() * 4);
-  take(hp.halo_src.size() * 4);
-  take(hp.partial_halo.size() * 4);
-  take((size_t)std::max<int64_t>(hp.n_halo(), 1) * kMaxRegions * sizeof(int32_t));
+  take(hp.halo_rec.size() * 4);
+  take(hp.halo_node.size() * 4);
+  take((size_t)std::max<int64_t>(hp.n_partials, 1) * kMaxRegions * sizeof(int32_t));
   take((size_t)std::max<int64_t>(hp.n_partials, 1) * 4 * sizeof(double) * kMaxRegions);
   take((size_t)std::max<int64_t>(hp.n_tiles(), 1) * sizeof(double));
   take(16);
@@ -130,11 +128,9 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   const size_t o_sc = ab.take(hp.step_code.size() * 2);
   const size_t o_mf = ab.take(hp.step_mat_f.size() * 4);
   const size_t o_md = ab.take(hp.step_mat_d.size() * 8);
-  const size_t o_hi = ab.take(hp.halo_info.size() * 4);
-  const size_t o_hp = ab.take(hp.halo_ptr.size() * 4);
-  const size_t o_hs = ab.take(hp.halo_src.size() * 4);
-  const size_t o_ph = ab.take(hp.partial_halo.size() * 4);
-  const size_t o_hc = ab.take((size_t)std::max<int64_t>(hp.n_halo(), 1) * kMaxRegions * sizeof(int32_t));
+  const size_t o_hr = ab.take(hp.halo_rec.size() * 4);
+  const size_t o_hn = ab.take(hp.halo_node.size() * 4);
+  const size_t o_hc = ab.take((size_t)std::max<int64_t>(hp.n_partials, 1) * kMaxRegions * sizeof(int32_t));
   const size_t o_pa = ab.take((size_t)std::max<int64_t>(hp.n_partials, 1) * 4 * sizeof(double) * kMaxRegions);
   const size_t o_te = ab.take((size_t)std::max<int64_t>(nt, 1) * sizeof(double));
   const size_t o_inv = ab.take(16);
@@ -180,14 +176,13 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
       (st = upload(base, o_so, hp.slot_off, s)) || (st = upload(base, o_tc, hp.tile_cnt, s)) ||
       (st = upload(base, o_fh, hp.fan_head, s)) || (st = upload(base, o_sc, hp.step_code, s)) ||
       (st = upload(base, o_mf, hp.step_mat_f, s)) || (st = upload(base, o_md, hp.step_mat_d, s)) ||
-      (st = upload(base, o_hi, hp.halo_info, s)) || (st = upload(base, o_hp, hp.halo_ptr, s)) ||
-      (st = upload(base, o_hs, hp.halo_src, s)) || (st = upload(base, o_ph, hp.partial_halo, s)) ||
+      (st = upload(base, o_hr, hp.halo_rec, s)) || (st = upload(base, o_hn, hp.halo_node, s)) ||
       (st = upload(base, o_fe, fext, s)) ||
       (st = upload(base, o_ff, fext_f, s)) || (st = upload(base, o_dv, vals, s)) || (st = upload(base, o_dm, mask, s)))
     return fail(st);
   ce = cudaMemsetAsync(base + o_inv, 0, 16, s);
   if (ce == cudaSuccess)
-    ce = cudaMemsetAsync(base + o_hc, 0, (size_t)std::max<int64_t>(hp.n_halo(), 1) * kMaxRegions * sizeof(int32_t), s);
+    ce = cudaMemsetAsync(base + o_hc, 0, (size_t)std::max<int64_t>(hp.n_partials, 1) * kMaxRegions * sizeof(int32_t), s);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(base + o_rc, 0, 64, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);  // host vectors die at return
   if (ce != cudaSuccess) return fail(cuda_fail(ce, "mesh upload"));
@@ -212,10 +207,8 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   P.step_code = reinterpret_cast<const uint16_t*>(base + o_sc);
   P.step_mat_f = reinterpret_cast<const float2*>(base + o_mf);
   P.step_mat_d = reinterpret_cast<const double2*>(base + o_md);
-  P.halo_info = reinterpret_cast<const int32_t*>(base + o_hi);
-  P.halo_ptr = reinterpret_cast<const int32_t*>(base + o_hp);
-  P.halo_src = reinterpret_cast<const int32_t*>(base + o_hs);
-  P.partial_halo = reinterpret_cast<const int32_t*>(base + o_ph);
+  P.halo_rec = reinterpret_cast<const int4*>(base + o_hr);
+  P.halo_node = reinterpret_cast<const int4*>(base + o_hn);
   P.halo_count = reinterpret_cast<int32_t*>(base + o_hc);
   P.partial = base + o_pa;
   P.tile_energy = reinterpret_cast<double*>(base + o_te);

@@ -58,7 +58,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, unsigned int& gen, int*
 }
 
 template <int DIM, int KIND>
-__global__ void __launch_bounds__(kThreads) pcg_persistent_kernel(DevPlan P, PersistArgs A) {
+__global__ void __launch_bounds__(kThreads, 2) pcg_persistent_kernel(DevPlan P, PersistArgs A) {
   extern __shared__ __align__(32) unsigned char smem[];
   __shared__ double scratch[16];
   __shared__ double s_beta, s_alpha;
@@ -79,23 +79,30 @@ __global__ void __launch_bounds__(kThreads) pcg_persistent_kernel(DevPlan P, Per
   __syncthreads();
   if (s_stop) return;  // uniform: written before the launch
 
-  OpArgs oa{};
-  oa.u = A.u;
-  oa.y = A.q;
-  oa.load_scale = 1.0;
-  oa.pcg.r = A.r;
-  oa.pcg.dinv = A.dinv;
-  oa.pcg.p[0] = A.p[0];
-  oa.pcg.p[1] = A.p[1];
-  oa.pcg.st = st;
-  oa.pcg.tile_part = A.tile_part;
-  oa.pcg.ticket = A.ticket;
+  // the apply's arguments live in shared memory (read by every thread, kept out of registers)
+  __shared__ OpArgs oa;
+  if (threadIdx.x == 0) {
+    oa = OpArgs{};
+    oa.u = A.u;
+    oa.y = A.q;
+    oa.load_scale = 1.0;
+    oa.pcg.r = A.r;
+    oa.pcg.dinv = A.dinv;
+    oa.pcg.p[0] = A.p[0];
+    oa.pcg.p[1] = A.p[1];
+    oa.pcg.st = st;
+    oa.pcg.tile_part = A.tile_part;
+    oa.pcg.ticket = A.ticket;
+  }
   bool ok = true;
   for (;;) {
     // ---- A: direction, q = A p, tile sums of p_e . A_e p_e, alpha by the last tile
     const int odd = s_iter & 1;
-    oa.pcg.beta = s_beta;
-    oa.pcg.odd = odd;
+    if (threadIdx.x == 0) {
+      oa.pcg.beta = s_beta;
+      oa.pcg.odd = odd;
+    }
+    __syncthreads();
     for (int t = blockIdx.x; t < P.n_tiles; t += gridDim.x) {
       process_tile<DIM, KIND, OPS, double, float>(P, oa, t, smem, L);
       __syncthreads();
@@ -114,7 +121,7 @@ __global__ void __launch_bounds__(kThreads) pcg_persistent_kernel(DevPlan P, Per
       const double* p = odd ? A.p[0] : A.p[1];  // the direction just formed
       for (int vb = blockIdx.x; vb < kReduceBlocks; vb += gridDim.x) {
         double v[2] = {0.0, 0.0};
-        pcg_update_range(A.n, A.x, A.r, p, A.q, A.dinv, alpha, vb, v);
+        pcg_update_range<2>(A.n, A.x, A.r, p, A.q, A.dinv, alpha, vb, v);
         if (grid_sum_v<2>(v, A.red_part, A.red_counter, scratch, vb, kReduceBlocks) && threadIdx.x == 0)
           pcg_finish_update(st, v[0], v[1]);
       }

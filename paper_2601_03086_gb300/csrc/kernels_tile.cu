@@ -5,8 +5,16 @@
 
 namespace pfem {
 
+// Resident CTAs per SM the register allocation must allow: 4 for the FP32 linear operator
+// (more tiles in flight hide the staging and halo latencies), fewer where the arithmetic
+// needs more registers (Neo-Hookean, FP64).
+template <int KIND, typename CT>
+constexpr int tile_min_blocks() {
+  return sizeof(CT) == 8 ? 1 : (KIND == K_LIN ? 4 : 3);
+}
+
 template <int DIM, int KIND, int OPS, typename VT, typename CT>
-__global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
+__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<KIND, CT>()) tile_kernel(DevPlan P, OpArgs A) {
   extern __shared__ __align__(32) unsigned char smem[];
   constexpr bool NEED_U = (OPS & (OP_RESIDUAL | OP_ENERGY)) || (KIND == K_NH && (OPS & (OP_TANGENT | OP_DIAG)));
   constexpr bool NEED_V = (OPS & OP_TANGENT) != 0;
@@ -17,7 +25,7 @@ __global__ void __launch_bounds__(kThreads) tile_kernel(DevPlan P, OpArgs A) {
 // Ragged batch of 3-D meshes in one launch: CTA b runs tile btile[b].y of mesh btile[b].x
 // (FP32 vectors and arithmetic; linear or Neo-Hookean chosen per mesh, uniform per CTA).
 template <int OPS>
-__global__ void __launch_bounds__(kThreads) batch_kernel(BatchDev B, OpArgs A) {
+__global__ void __launch_bounds__(kTileThreads) batch_kernel(BatchDev B, OpArgs A) {
   extern __shared__ __align__(32) unsigned char smem[];
   __shared__ DevPlan sP;
   const int2 bt = B.btile[blockIdx.x];
@@ -71,7 +79,7 @@ static pfem_status run_batch(const BatchDev& B, const OpArgs& A, int n_blocks, c
   static int max_dyn = 0;
   pfem_status st = allow_dynamic_smem(batch_kernel<OPS>, L.total, &max_dyn);
   if (st) return st;
-  batch_kernel<OPS><<<n_blocks, kThreads, L.total, s>>>(B, A);
+  batch_kernel<OPS><<<n_blocks, kTileThreads, L.total, s>>>(B, A);
   PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
@@ -102,7 +110,7 @@ pfem_status launch_batch(const BatchDev& B, int n_blocks, int n_meshes, const fl
 
 // ---- serving: one shared PCG step over all resident solves ------------------------------
 
-__global__ void __launch_bounds__(kThreads) serve_apply_kernel(const ReqDev* reqs, const int2* btile, int max_local,
+__global__ void __launch_bounds__(kTileThreads) serve_apply_kernel(const ReqDev* reqs, const int2* btile, int max_local,
                                                                int slot_cap, int step_cap) {
   extern __shared__ __align__(32) unsigned char smem[];
   __shared__ ReqDev sR;
@@ -185,13 +193,43 @@ pfem_status launch_serve_step(const ReqDev* reqs, const int2* btile, int n_apply
   pfem_status st = allow_dynamic_smem(serve_apply_kernel, L.total, &max_dyn);
   if (st) return st;
   if (n_apply_blocks > 0) {
-    serve_apply_kernel<<<n_apply_blocks, kThreads, L.total, s>>>(reqs, btile, max_local, slot_cap, step_cap);
+    serve_apply_kernel<<<n_apply_blocks, kTileThreads, L.total, s>>>(reqs, btile, max_local, slot_cap, step_cap);
     PFEM_COUNT_LAUNCH();
   }
   if (n_update_blocks > 0) {
     serve_update_kernel<<<n_update_blocks, 256, 0, s>>>(reqs, ublk);
     PFEM_COUNT_LAUNCH();
   }
+  PFEM_CUDA(cudaGetLastError());
+  return PFEM_OK;
+}
+
+// Halo nodes of region `region` after a tile launch with defer_halo: each thread sums one
+// node's partials in ascending tile order (the order the in-tile completion uses, so the
+// result is the same bit for bit) and writes the output.
+template <int DIM, int OUT, typename VT, typename CT>
+__global__ void __launch_bounds__(256) halo_finish_kernel(DevPlan P, OpArgs A, int region) {
+  const int h = blockIdx.x * blockDim.x + threadIdx.x;
+  if (h >= P.n_halo) return;
+  const CT* part = static_cast<const CT*>(P.partial) + (size_t)region * P.n_partials * 4;
+  const CT sc = A.out_scale ? CT(*A.out_scale) : CT(1);
+  const int4 rec = P.halo_node[h];
+  CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
+  for (int k = rec.x; k < rec.x + rec.y; ++k) {
+    CT t[4];
+    ld4(part + 4 * (size_t)k, t);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) sum[i] += t[i];
+  }
+  const unsigned info = (unsigned)rec.z;
+  final_write<DIM, OUT, VT, CT>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, sum, sc);
+}
+
+template <int DIM, int OUT, typename VT, typename CT>
+static pfem_status finish_halo(const DevPlan& P, const OpArgs& A, int region, cudaStream_t s) {
+  if (P.n_halo <= 0) return PFEM_OK;
+  halo_finish_kernel<DIM, OUT, VT, CT><<<(P.n_halo + 255) / 256, 256, 0, s>>>(P, A, region);
+  PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }
@@ -205,9 +243,20 @@ static pfem_status run(const DevPlan& P, const OpArgs& A, cudaStream_t s) {
   static int max_dyn = 0;  // per instantiation
   pfem_status st = allow_dynamic_smem(tile_kernel<DIM, KIND, OPS, VT, CT>, L.total, &max_dyn);
   if (st) return st;
-  tile_kernel<DIM, KIND, OPS, VT, CT><<<P.n_tiles, kThreads, L.total, s>>>(P, A);
+  OpArgs a = A;
+  a.defer_halo = ((OPS & OP_PCG) == 0 && P.n_partials >= kDeferHaloPartials) ? 1 : 0;
+  tile_kernel<DIM, KIND, OPS, VT, CT><<<P.n_tiles, kTileThreads, L.total, s>>>(P, a);
   PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
+  if (!a.defer_halo) return PFEM_OK;
+  int region = 0;  // regions in the order the tile kernel fills them
+  if constexpr ((OPS & OP_RESIDUAL) != 0)
+    if ((st = finish_halo<DIM, OUT_RES, VT, CT>(P, a, region++, s))) return st;
+  if constexpr ((OPS & OP_TANGENT) != 0)
+    if ((st = finish_halo<DIM, OUT_TAN, VT, CT>(P, a, region++, s))) return st;
+  if constexpr ((OPS & OP_DIAG) != 0)
+    if ((st = finish_halo<DIM, OUT_DIAG, VT, CT>(P, a, region++, s))) return st;
+  (void)region;
   return PFEM_OK;
 }
 

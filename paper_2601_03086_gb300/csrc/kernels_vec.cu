@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kReduceThreads)
   const double alpha = st->alpha;
   const double* p = ((st->iter + 1) & 1) ? p1 : p0;
   double v[2] = {0.0, 0.0};
-  pcg_update_range(n, x, r, p, q, dinv, alpha, blockIdx.x, v);  // launched as kReduceBlocks x kReduceThreads
+  pcg_update_range<4>(n, x, r, p, q, dinv, alpha, blockIdx.x, v);  // launched as kReduceBlocks x kReduceThreads
   if (grid_sum<2>(v, partials, counter, scratch) && threadIdx.x == 0) {
     pcg_finish_update(st, v[0], v[1]);
     if (set_cond) cudaGraphSetConditional(cond, (st->done == 0 && st->repl == 0) ? 1u : 0u);

@@ -35,16 +35,17 @@ __device__ __forceinline__ void pcg_finish_update(PcgState* st, double rz, doubl
 // The vector part of the update for the DOFs of reduction block vb (of kReduceBlocks x
 // kReduceThreads; thread t takes i = vb * 256 + t + k * S, S = 296 * 256, in k order):
 // x += alpha p, r -= alpha q, and r.z, r.r of the new residual accumulated into v. Loads of
-// four consecutive k are issued before their arithmetic; the arithmetic and its order are
-// those of the plain loop. r, p, q go through L2 only (other CTAs of a persistent launch
-// write them).
+// U consecutive k are issued before their arithmetic; the arithmetic and its order are those
+// of the plain loop (any U gives the same bits). r, p, q go through L2 only (other CTAs of a
+// persistent launch write them).
+template <int U>
 __device__ __forceinline__ void pcg_update_range(int64_t n, double* x, double* r, const double* p, const double* q,
                                                  const double* dinv, double alpha, int vb, double (&v)[2]) {
   const int64_t S = (int64_t)kReduceBlocks * kReduceThreads;
-  for (int64_t i = (int64_t)vb * kReduceThreads + threadIdx.x; i < n; i += 4 * S) {
-    double pp[4], qq[4], rr[4], dd[4], xx[4];
+  for (int64_t i = (int64_t)vb * kReduceThreads + threadIdx.x; i < n; i += U * S) {
+    double pp[U], qq[U], rr[U], dd[U], xx[U];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < U; ++j) {
       const int64_t k = i + j * S;
       if (k < n) {
         pp[j] = __ldcg(p + k);
@@ -55,7 +56,7 @@ __device__ __forceinline__ void pcg_update_range(int64_t n, double* x, double* r
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < U; ++j) {
       const int64_t k = i + j * S;
       if (k < n) {
         x[k] = xx[j] + alpha * pp[j];

@@ -30,7 +30,10 @@
 //                 stored step-major inside the tile: s = step_begin + sum_{j<i} cnt_j + f,
 //                 so a warp's fans read consecutive records at every step
 //   info        = node id (bits 0-27) | Dirichlet mask of DOF i at bit 28+i
-//   halo_info[h], halo_ptr[h..h+1], halo_src[k]: halo nodes (sorted by id) and the indices
+//   halo_rec[i]  = {slot, first, count, info} of the i-th (tile, halo node) pair in tile order:
+//                 the node's partials occupy [first, first + count) in ascending tile order, this
+//                 tile's at `slot`; the last tile to publish sums that range (ticket at `first`)
+//   halo_info[h], halo_ptr[h..h+1], halo_src[k] (host): halo nodes (sorted by id) and the indices
 //                of their partials in ascending tile order
 #pragma once
 
@@ -54,7 +57,8 @@ constexpr int kTileNodes = 1024;   // max distinct nodes per tile (10-bit local 
 constexpr int kMaxRank = 63;       // max incidences of one node inside one tile (6 bits)
 constexpr int kInfoIdBits = 28;
 constexpr uint32_t kInfoIdMask = (1u << kInfoIdBits) - 1u;
-constexpr int kThreads = 256;      // threads per tile CTA
+constexpr int kThreads = 256;      // threads per CTA of the persistent PCG kernel
+constexpr int kTileThreads = 256;  // threads per element-tile CTA (tile, batch and serving kernels)
 constexpr int kMaxRegions = 3;     // output ops one tile launch can produce (partials/tickets each)
 constexpr int kReduceBlocks = 296; // fixed grid of the deterministic FP64 reductions (2 x 148)
 
@@ -95,6 +99,8 @@ struct HostPlan {
   int64_t n_partials = 0;
   std::vector<int32_t> elem_perm; // original element id of each step
   std::vector<int32_t> partial_halo; // halo node index of each partial
+  std::vector<int32_t> halo_rec;     // 4 per partial (see halo_rec above)
+  std::vector<int32_t> halo_node;    // 4 per halo node: {first, count, info, 0}
   int64_t n_tiles() const { return (int64_t)tile_a.size() / 4; }
   int64_t n_local() const { return (int64_t)slot_off.size(); }
   int64_t n_halo() const { return (int64_t)halo_info.size(); }
@@ -136,11 +142,10 @@ struct DevPlan {
   const uint16_t* step_code;
   const float2* step_mat_f;
   const double2* step_mat_d;
-  const int32_t* halo_info;
-  const int32_t* halo_ptr;
-  const int32_t* halo_src;
-  const int32_t* partial_halo;  // halo node index of each partial
-  int32_t* halo_count;   // per region x halo node: partials published so far (reset by the last)
+  const int4* halo_rec;  // per (tile, halo node) pair in tile order
+  const int4* halo_node; // per halo node {first partial, count, info, 0}
+  int32_t* halo_count;   // per region x partial slot (used at each halo node's first slot):
+                         // partials published so far (reset by the last)
   void* partial;         // scratch: per region n_partials slots of 4 compute-type values
   double* tile_energy;   // per-tile strain-energy partials
   int32_t* inverted;     // count of J <= 0 elements (device int)
@@ -241,6 +246,7 @@ struct OpArgs {
   PcgArgs pcg;      // OP_PCG only
   const float* out_scale;  // device scalar multiplying residual / tangent outputs (null = 1)
   int hess;                // tangent on prescribed DOFs: 0 = identity block (y = v), 1 = zero
+  int defer_halo;          // 1: tiles only publish halo partials; halo_finish_kernel completes them
 };
 
 // A ragged batch of meshes evaluated in one launch (batch.cu builds it).
@@ -290,6 +296,10 @@ pfem_status launch_element_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dty
 // Launches the persistent PCG kernel (FP32 element arithmetic only); PFEM_ERR_UNSUPPORTED
 // when it cannot run here (other arithmetic, no co-resident grid), without side effects.
 pfem_status launch_pcg_persistent(const DevPlan& P, pfem_dtype ct, const PersistArgs& a, cudaStream_t s);
+
+// Halo partials from which launch_element_op completes halo nodes in a separate pass instead
+// of inside the tiles (removes the per-tile fence / ticket / reload chain; costs a launch).
+constexpr int64_t kDeferHaloPartials = 1 << 18;
 
 // Dynamic shared memory one tile CTA of launch_element_op needs.
 size_t element_op_smem(const DevPlan& P, int ops, pfem_dtype ct);

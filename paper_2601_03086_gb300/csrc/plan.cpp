@@ -65,14 +65,14 @@ static bool finite_all(const double* p, int64_t n) {
   return true;
 }
 
-// Tile size: 1024 elements once the mesh fills the GPU several times over (longer fans and
-// fewer halo partials per element); smaller tiles for small meshes so that at least ~4 tiles
-// land on each of the 152 SMs.
+// Tile size: 768 elements once the mesh fills the GPU several times over (longer fans and
+// fewer halo partials per element, while four tiles still fit on an SM); smaller tiles for
+// small meshes so that at least ~4 tiles land on each of the 152 SMs.
 int default_tile_elems(int64_t n_elems) {
   const int64_t per = (n_elems + 152 * 4 - 1) / (152 * 4);
   int64_t t = (per + 63) / 64 * 64;
   if (t < 256) t = 256;
-  if (t > 1024) t = 1024;
+  if (t > 768) t = 768;
   return (int)t;
 }
 
@@ -530,9 +530,23 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
   for (auto& pr : halo_pairs) P->halo_src[(size_t)(start[pr.first] + fill[pr.first]++)] = pr.second;
   P->n_partials = n_partials;
   P->partial_halo.assign((size_t)n_partials, 0);
+  P->halo_rec.assign((size_t)n_partials * 4, 0);
+  P->halo_node.assign((size_t)P->n_halo() * 4, 0);
+  for (int64_t h = 0; h < P->n_halo(); ++h) {
+    P->halo_node[(size_t)h * 4] = P->halo_ptr[(size_t)h];
+    P->halo_node[(size_t)h * 4 + 1] = P->halo_ptr[(size_t)h + 1] - P->halo_ptr[(size_t)h];
+    P->halo_node[(size_t)h * 4 + 2] = P->halo_info[(size_t)h];
+  }
   for (int64_t h = 0; h < P->n_halo(); ++h)
-    for (int32_t k = P->halo_ptr[(size_t)h]; k < P->halo_ptr[(size_t)h + 1]; ++k)
-      P->partial_halo[(size_t)P->halo_src[(size_t)k]] = (int32_t)h;
+    for (int32_t k = P->halo_ptr[(size_t)h]; k < P->halo_ptr[(size_t)h + 1]; ++k) {
+      const int32_t pi = P->halo_src[(size_t)k];
+      P->partial_halo[(size_t)pi] = (int32_t)h;
+      int32_t* rec = &P->halo_rec[(size_t)pi * 4];
+      rec[0] = k;
+      rec[1] = P->halo_ptr[(size_t)h];
+      rec[2] = P->halo_ptr[(size_t)h + 1] - P->halo_ptr[(size_t)h];
+      rec[3] = P->halo_info[(size_t)h];
+    }
 
   // ---- external force ---------------------------------------------------------------------
   f_ext->assign((size_t)(N * dim), 0.0);
@@ -691,8 +705,13 @@ pfem_status verify_plan(const pfem_mesh_desc* d, const HostPlan& P) {
       deg += (int)partial_deg_of[(size_t)pi];
     }
     if (deg != gdeg[(size_t)gid]) return bad("halo node incidences", gid, deg);
-    for (int k = b; k < e; ++k)
-      if (P.partial_halo[(size_t)P.halo_src[(size_t)k]] != (int32_t)h) return bad("partial -> halo map", gid, k);
+    for (int k = b; k < e; ++k) {
+      const int32_t pi = P.halo_src[(size_t)k];
+      if (P.partial_halo[(size_t)pi] != (int32_t)h) return bad("partial -> halo map", gid, k);
+      const int32_t* rec = &P.halo_rec[(size_t)pi * 4];
+      if (rec[0] != k || rec[1] != b || rec[2] != e - b || rec[3] != P.halo_info[(size_t)h])
+        return bad("halo record", gid, k);
+    }
     if (gdeg[(size_t)gid] == 0) return bad("orphan node in the halo list", gid, h);
   }
   for (int64_t n = 0; n < N; ++n)

@@ -112,8 +112,7 @@ __device__ __forceinline__ double pcg_direction(const PcgArgs& g, const double* 
 
 template <int DIM, int OUT, typename VT, typename CT, bool PCG = false>
 __device__ __forceinline__ void final_write(const DevPlan& P, const OpArgs& A, int64_t gid, unsigned mask,
-                                            const CT (&acc)[4]) {
-  const CT sc = A.out_scale ? CT(*A.out_scale) : CT(1);  // upstream factor (batched autograd)
+                                            const CT (&acc)[4], CT sc) {
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
     const int64_t k = gid * DIM + i;
@@ -361,8 +360,11 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
   const int* sinfo = reinterpret_cast<const int*>(smem + L.info);
   const CT* slot = reinterpret_cast<const CT*>(smem + L.slot);
   CT* part = static_cast<CT*>(P.partial) + (size_t)region * P.n_partials * 4;
-  int32_t* count = P.halo_count + (size_t)region * P.n_halo;
+  int32_t* count = P.halo_count + (size_t)region * P.n_partials;
+  const CT sc = A.out_scale ? CT(*A.out_scale) : CT(1);  // upstream factor (batched autograd)
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+    int slot_i = 0;
+    if (l >= ncomp) slot_i = P.halo_rec[pbeg + l - ncomp].x;  // issued before the slot sums
     const int b = soff[l], e = soff[l + 1];
     CT acc[4] = {CT(0), CT(0), CT(0), CT(0)};
     for (int k = b; k < e; ++k) {
@@ -373,12 +375,13 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
     }
     if (l < ncomp) {
       const unsigned info = (unsigned)sinfo[l];
-      final_write<DIM, OUT, VT, CT, PCG>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, acc);
+      final_write<DIM, OUT, VT, CT, PCG>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, acc, sc);
       continue;
     }
-    // halo node: publish this tile's partial
-    st4(part + 4 * (size_t)(pbeg + l - ncomp), acc[0], acc[1], acc[2], CT(0));
+    // halo node: publish this tile's partial in the node's contiguous range
+    st4(part + 4 * (size_t)slot_i, acc[0], acc[1], acc[2], CT(0));
   }
+  if (A.defer_halo) return;  // uniform: halo_finish_kernel completes the halo nodes
   // Release once per tile: every partial of this tile is visible device-wide before any of
   // its tickets; the tile whose ticket completes a halo node's set (acquire fence after the
   // ticket) sums that node's partials in ascending tile order and writes the output.
@@ -386,18 +389,17 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
   if (threadIdx.x == 0) __threadfence();
   __syncthreads();
   for (int l = ncomp + threadIdx.x; l < nl; l += blockDim.x) {
-    const int h = P.partial_halo[pbeg + l - ncomp];
-    const int pb = P.halo_ptr[h], pe = P.halo_ptr[h + 1];
-    if (atomicAdd(count + h, 1) == pe - pb - 1) {
+    const int4 rec = P.halo_rec[pbeg + l - ncomp];
+    if (atomicAdd(count + rec.y, 1) == rec.z - 1) {
       __threadfence();
       CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
-      for (int k = pb; k < pe; ++k) {
+      for (int k = rec.y; k < rec.y + rec.z; ++k) {
         CT t[4];
-        ldcg4(part + 4 * (size_t)P.halo_src[k], t);
+        ldcg4(part + 4 * (size_t)k, t);
 #pragma unroll
         for (int i = 0; i < DIM; ++i) sum[i] += t[i];
       }
-      const unsigned hinfo = (unsigned)P.halo_info[h];
+      const unsigned hinfo = (unsigned)rec.w;
       const int64_t hgid = (int64_t)(hinfo & kInfoIdMask);
       if constexpr (PCG) {  // the node's new direction, as every tile staged it
 #pragma unroll
@@ -406,8 +408,8 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
           p_new[k] = pcg_direction(A.pcg, p_old, beta, k, ((hinfo >> kInfoIdBits) >> i) & 1u);
         }
       }
-      final_write<DIM, OUT, VT, CT, PCG>(P, A, hgid, hinfo >> kInfoIdBits, sum);
-      count[h] = 0;
+      final_write<DIM, OUT, VT, CT, PCG>(P, A, hgid, hinfo >> kInfoIdBits, sum, sc);
+      count[rec.y] = 0;
     }
   }
 }
@@ -446,7 +448,8 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
     p_new = odd ? A.pcg.p[0] : A.pcg.p[1];
   }
 
-  // ---- stage tile nodes
+  // ---- stage the tile in shared memory; every round issues all its global loads before
+  // its shared stores (the step records first: they depend on nothing)
   {
     CT* sx = reinterpret_cast<CT*>(smem + L.x);
     CT* su = reinterpret_cast<CT*>(smem + L.u);
@@ -455,53 +458,91 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
     int* sinfo = reinterpret_cast<int*>(smem + L.info);
     const VT* u = static_cast<const VT*>(A.u);
     const VT* v = static_cast<const VT*>(A.v);
-    for (int l = threadIdx.x; l < nl; l += blockDim.x) {
-      const float4 rf = P.lnode_f[lbeg + l];
-      const int info = __float_as_int(rf.w);
-      if constexpr (sizeof(CT) == 4) {
-        st4(sx + 4 * l, rf.x, rf.y, rf.z, 0.f);
-      } else {
-        const PfemDouble4 rd = P.lnode_d[lbeg + l];
-        st4(sx + 4 * l, rd.x, rd.y, rd.z, 0.0);
-      }
-      sinfo[l] = info;
-      soff[l] = (int)P.slot_off[lbeg + l];
-      const int64_t gid = (int64_t)((unsigned)info & kInfoIdMask);
-      const unsigned mask = (unsigned)info >> kInfoIdBits;
-      if constexpr (NEED_U) {
-        CT w[3] = {CT(0), CT(0), CT(0)};
+    {  // fan heads and step records (coalesced; read from shared memory by the fans)
+      using M2 = typename std::conditional<sizeof(CT) == 4, float2, double2>::type;
+      const M2* gmat = reinterpret_cast<const M2*>(sizeof(CT) == 4 ? static_cast<const void*>(P.step_mat_f)
+                                                                   : static_cast<const void*>(P.step_mat_d));
+      M2* smat = reinterpret_cast<M2*>(smem + L.smat);
+      ushort4* shead = reinterpret_cast<ushort4*>(smem + L.head);
+      uint16_t* scode = reinterpret_cast<uint16_t*>(smem + L.scode);
+      for (int j0 = threadIdx.x; j0 < ns; j0 += 4 * blockDim.x) {
+        uint16_t c[4];
+        M2 m[4];
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) w[i] = CT(u[gid * DIM + i]);
-        st4(su + 4 * l, w[0], w[1], w[2], CT(0));
-      }
-      if constexpr (PCG) {
-        CT w[3] = {CT(0), CT(0), CT(0)};
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) {
-          const int64_t k = gid * DIM + i;
-          const double pn = pcg_direction(A.pcg, p_old, beta, k, (mask >> i) & 1u);
-          if (l < ncomp) p_new[k] = pn;  // complete nodes: this tile owns the DOF
-          w[i] = CT(pn);
+        for (int q = 0; q < 4; ++q) {
+          const int j = j0 + q * (int)blockDim.x;
+          if (j < ns) {
+            c[q] = P.step_code[sbeg + j];
+            m[q] = gmat[sbeg + j];
+          }
         }
-        st4(sv + 4 * l, w[0], w[1], w[2], CT(0));
-      } else if constexpr (NEED_V) {
-        CT w[3] = {CT(0), CT(0), CT(0)};
 #pragma unroll
-        for (int i = 0; i < DIM; ++i) w[i] = ((mask >> i) & 1u) ? CT(0) : CT(v[gid * DIM + i]);
-        st4(sv + 4 * l, w[0], w[1], w[2], CT(0));
+        for (int q = 0; q < 4; ++q) {
+          const int j = j0 + q * (int)blockDim.x;
+          if (j < ns) {
+            scode[j] = c[q];
+            smat[j] = m[q];
+          }
+        }
+      }
+      for (int j = threadIdx.x; j < nf; j += blockDim.x) shead[j] = P.fan_head[fbeg + j];
+    }
+    // nodes, two per thread and round: records first, then the gathers their ids select
+    for (int l0 = threadIdx.x; l0 < nl; l0 += 2 * blockDim.x) {
+      const int ls[2] = {l0, l0 + (int)blockDim.x};
+      float4 rf[2];
+      int so[2] = {0, 0};
+      CT xc[2][3];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (ls[q] >= nl) continue;
+        rf[q] = P.lnode_f[lbeg + ls[q]];
+        so[q] = (int)P.slot_off[lbeg + ls[q]];
+        if constexpr (sizeof(CT) == 4) {
+          xc[q][0] = rf[q].x, xc[q][1] = rf[q].y, xc[q][2] = rf[q].z;
+        } else {
+          const PfemDouble4 rd = P.lnode_d[lbeg + ls[q]];
+          xc[q][0] = rd.x, xc[q][1] = rd.y, xc[q][2] = rd.z;
+        }
+      }
+      CT wu[2][3], wv[2][3];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) wu[q][i] = wv[q][i] = CT(0);
+        if (ls[q] >= nl) continue;
+        const unsigned info = (unsigned)__float_as_int(rf[q].w);
+        const int64_t gid = (int64_t)(info & kInfoIdMask);
+        const unsigned mask = info >> kInfoIdBits;
+        if constexpr (NEED_U) {
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) wu[q][i] = CT(u[gid * DIM + i]);
+        }
+        if constexpr (PCG) {
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) {
+            const int64_t k = gid * DIM + i;
+            const double pn = pcg_direction(A.pcg, p_old, beta, k, (mask >> i) & 1u);
+            if (ls[q] < ncomp) p_new[k] = pn;  // complete nodes: this tile owns the DOF
+            wv[q][i] = CT(pn);
+          }
+        } else if constexpr (NEED_V) {
+#pragma unroll
+          for (int i = 0; i < DIM; ++i) wv[q][i] = ((mask >> i) & 1u) ? CT(0) : CT(v[gid * DIM + i]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int l = ls[q];
+        if (l >= nl) continue;
+        st4(sx + 4 * l, xc[q][0], xc[q][1], xc[q][2], CT(0));
+        sinfo[l] = __float_as_int(rf[q].w);
+        soff[l] = so[q];
+        if constexpr (NEED_U) st4(su + 4 * l, wu[q][0], wu[q][1], wu[q][2], CT(0));
+        if constexpr (NEED_V) st4(sv + 4 * l, wv[q][0], wv[q][1], wv[q][2], CT(0));
       }
     }
     if (threadIdx.x == 0) soff[nl] = nf * DIM + ns;  // slots: DIM + k per fan
-    {  // the tile's fan heads and step records (coalesced; read from shared memory by the fans)
-      ushort4* shead = reinterpret_cast<ushort4*>(smem + L.head);
-      uint16_t* scode = reinterpret_cast<uint16_t*>(smem + L.scode);
-      for (int j = threadIdx.x; j < nf; j += blockDim.x) shead[j] = P.fan_head[fbeg + j];
-      for (int j = threadIdx.x; j < ns; j += blockDim.x) {
-        scode[j] = P.step_code[sbeg + j];
-        if constexpr (sizeof(CT) == 4) reinterpret_cast<float2*>(smem + L.smat)[j] = P.step_mat_f[sbeg + j];
-        else reinterpret_cast<double2*>(smem + L.smat)[j] = P.step_mat_d[sbeg + j];
-      }
-    }
     if (threadIdx.x < kMaxFan) {  // fan counts per step (8 x uint16 in one uint4)
       const uint4 c = P.tile_cnt[t];
       const unsigned q = threadIdx.x >> 1;
