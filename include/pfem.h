@@ -194,13 +194,13 @@ pfem_status pfem_solve_newton(pfem_mesh_t mesh, pfem_dtype dtype, const double* 
                               double* u_out, pfem_solve_info* info);
 
 /* Solver loop style for later solves (process-wide); every mode gives bitwise identical
- * iterates. 0 (default): one persistent cooperative kernel runs PCG iterations until an FP64
+ * iterates. 0: one persistent cooperative kernel runs PCG iterations until an FP64
  * residual replacement or termination (grid barriers with bounded waits: a barrier that
  * gives up ends the solve with PFEM_ERR_TIMEOUT); FP64 element arithmetic, or a device that
  * cannot hold the grid, uses mode 2 instead. 1: the two kernels of one iteration at a time
  * with a host-synchronised convergence check (the plain GPU loop used as the serving
- * baseline). 2: the iteration captured as a CUDA graph with a device-side while loop.
- * Other values: PFEM_ERR_INVALID_ARG. */
+ * baseline). 2 (default): the iteration captured as a CUDA graph with a device-side while
+ * loop. Other values: PFEM_ERR_INVALID_ARG. */
 pfem_status pfem_set_solver_mode(int32_t mode);
 
 /* ---- ragged batch: energy loss, gradient and Hessian-vector product in one launch --- */

@@ -83,6 +83,7 @@ size_t mesh_arena_bytes(const HostPlan& hp) {
   take(hp.step_mat_d.size() * 8);
   take(hp.halo_rec.size() * 4);
   take(hp.halo_node.size() * 4);
+  take(hp.halo_seq.size() * 4);
   take((size_t)std::max<int64_t>(hp.n_partials, 1) * kMaxRegions * sizeof(int32_t));
   take((size_t)std::max<int64_t>(hp.n_partials, 1) * 4 * sizeof(double) * kMaxRegions);
   take((size_t)std::max<int64_t>(hp.n_tiles(), 1) * sizeof(double));
@@ -130,6 +131,7 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   const size_t o_md = ab.take(hp.step_mat_d.size() * 8);
   const size_t o_hr = ab.take(hp.halo_rec.size() * 4);
   const size_t o_hn = ab.take(hp.halo_node.size() * 4);
+  const size_t o_hq = ab.take(hp.halo_seq.size() * 4);
   const size_t o_hc = ab.take((size_t)std::max<int64_t>(hp.n_partials, 1) * kMaxRegions * sizeof(int32_t));
   const size_t o_pa = ab.take((size_t)std::max<int64_t>(hp.n_partials, 1) * 4 * sizeof(double) * kMaxRegions);
   const size_t o_te = ab.take((size_t)std::max<int64_t>(nt, 1) * sizeof(double));
@@ -177,6 +179,7 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
       (st = upload(base, o_fh, hp.fan_head, s)) || (st = upload(base, o_sc, hp.step_code, s)) ||
       (st = upload(base, o_mf, hp.step_mat_f, s)) || (st = upload(base, o_md, hp.step_mat_d, s)) ||
       (st = upload(base, o_hr, hp.halo_rec, s)) || (st = upload(base, o_hn, hp.halo_node, s)) ||
+      (st = upload(base, o_hq, hp.halo_seq, s)) ||
       (st = upload(base, o_fe, fext, s)) ||
       (st = upload(base, o_ff, fext_f, s)) || (st = upload(base, o_dv, vals, s)) || (st = upload(base, o_dm, mask, s)))
     return fail(st);
@@ -209,6 +212,7 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   P.step_mat_d = reinterpret_cast<const double2*>(base + o_md);
   P.halo_rec = reinterpret_cast<const int4*>(base + o_hr);
   P.halo_node = reinterpret_cast<const int4*>(base + o_hn);
+  P.halo_seq = reinterpret_cast<const int32_t*>(base + o_hq);
   P.halo_count = reinterpret_cast<int32_t*>(base + o_hc);
   P.partial = base + o_pa;
   P.tile_energy = reinterpret_cast<double*>(base + o_te);

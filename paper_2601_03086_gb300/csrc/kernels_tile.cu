@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) halo_finish_kernel(DevPlan P, OpArgs A, i
   CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
   for (int k = rec.x; k < rec.x + rec.y; ++k) {
     CT t[4];
-    ld4(part + 4 * (size_t)k, t);
+    ld4(part + 4 * (size_t)P.halo_seq[k], t);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) sum[i] += t[i];
   }

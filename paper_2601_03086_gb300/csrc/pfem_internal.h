@@ -101,6 +101,7 @@ struct HostPlan {
   std::vector<int32_t> partial_halo; // halo node index of each partial
   std::vector<int32_t> halo_rec;     // 4 per partial (see halo_rec above)
   std::vector<int32_t> halo_node;    // 4 per halo node: {first, count, info, 0}
+  std::vector<int32_t> halo_seq;     // per CSR position: tile-order index of the partial
   int64_t n_tiles() const { return (int64_t)tile_a.size() / 4; }
   int64_t n_local() const { return (int64_t)slot_off.size(); }
   int64_t n_halo() const { return (int64_t)halo_info.size(); }
@@ -143,7 +144,8 @@ struct DevPlan {
   const float2* step_mat_f;
   const double2* step_mat_d;
   const int4* halo_rec;  // per (tile, halo node) pair in tile order
-  const int4* halo_node; // per halo node {first partial, count, info, 0}
+  const int4* halo_node; // per halo node {first CSR position, count, info, 0}
+  const int32_t* halo_seq;  // per CSR position: tile-order index of its partial (deferred mode)
   int32_t* halo_count;   // per region x partial slot (used at each halo node's first slot):
                          // partials published so far (reset by the last)
   void* partial;         // scratch: per region n_partials slots of 4 compute-type values
@@ -174,7 +176,11 @@ enum : int {
   PCG_BREAKDOWN = 4,
   PCG_BARRIER_TIMEOUT = 6,  // a grid barrier of the persistent kernel gave up waiting
   PCG_STAGNATED = 7,        // the FP64 true residual stopped decreasing between replacements
+  PCG_NEGCURV = 8,          // p.Ap < 0 with truncate set: the iterate so far is the result
 };
+// Newton inner solves stop after this many PCG iterations at most (a tangent that is not
+// positive definite can keep plain CG from converging at all).
+constexpr int kInnerMaxIter = 20000;
 
 // Device-resident scalars of one Jacobi-PCG solve (FP64).
 struct PcgState {
@@ -191,7 +197,7 @@ struct PcgState {
   int done;               // PCG_* code, 0 while running
   int repl;               // 1 = stop the device loop for an FP64 residual replacement
   int replacements;
-  int pad;
+  int truncate;           // 1: stop at negative curvature after the first iteration (Newton inner solves)
 };
 
 // Extra inputs of the PCG-fused tangent apply (OP_PCG): the search direction is formed on
@@ -246,7 +252,8 @@ struct OpArgs {
   PcgArgs pcg;      // OP_PCG only
   const float* out_scale;  // device scalar multiplying residual / tangent outputs (null = 1)
   int hess;                // tangent on prescribed DOFs: 0 = identity block (y = v), 1 = zero
-  int defer_halo;          // 1: tiles only publish halo partials; halo_finish_kernel completes them
+  int defer_halo;          // 1: tiles publish halo partials in tile order (no loads, no tickets);
+                           // halo_finish_kernel completes them
 };
 
 // A ragged batch of meshes evaluated in one launch (batch.cu builds it).

@@ -531,6 +531,7 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* P, std::vector<double>
   P->n_partials = n_partials;
   P->partial_halo.assign((size_t)n_partials, 0);
   P->halo_rec.assign((size_t)n_partials * 4, 0);
+  P->halo_seq = P->halo_src;
   P->halo_node.assign((size_t)P->n_halo() * 4, 0);
   for (int64_t h = 0; h < P->n_halo(); ++h) {
     P->halo_node[(size_t)h * 4] = P->halo_ptr[(size_t)h];

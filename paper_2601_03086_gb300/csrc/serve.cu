@@ -42,11 +42,13 @@ double now_s() {
   return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-__global__ void init_state_kernel(PcgState* st, double tol, int max_iter, const double* ref_src, int done) {
+__global__ void init_state_kernel(PcgState* st, double tol, int max_iter, const double* ref_src, int done,
+                                  int truncate) {
   PcgState s;
   memset(&s, 0, sizeof(s));
   s.tol = tol;
   s.max_iter = max_iter;
+  s.truncate = truncate;
   s.repl_factor = 1e-2;
   s.ref = 1.0;
   if (ref_src) s.ref = *ref_src > 0.0 ? *ref_src : 1.0;
@@ -230,8 +232,8 @@ pfem_status enq_norm(Request* R, const double* v, double* out, cudaStream_t s) {
 // (Re)start PCG on A d = b from the current x: res = residual of the system at x, then
 // r = -res, rho, beta = 0 (replace kernel, restart) and both directions zero.
 pfem_status enq_pcg_start(Request* R, bool newton, double tol, const double* ref_src, cudaStream_t s) {
-  const int max_iter = (int)std::min<int64_t>(10 * R->n + 100, 1000000);
-  init_state_kernel<<<1, 1, 0, s>>>(R->st, tol, max_iter, ref_src, 0);
+  const int max_iter = (int)std::min<int64_t>(10 * R->n + 100, newton ? kInnerMaxIter : 1000000);
+  init_state_kernel<<<1, 1, 0, s>>>(R->st, tol, max_iter, ref_src, 0, newton ? 1 : 0);
   PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaMemsetAsync(R->p0, 0, (size_t)R->n * 8, s));
   PFEM_CUDA(cudaMemsetAsync(R->p1, 0, (size_t)R->n * 8, s));
@@ -279,7 +281,7 @@ pfem_status enq_newton_step(Request* R, cudaStream_t s) {
   if ((st = vk_lift(R->n, nullptr, R->mesh->plan.dvalues, R->mesh->plan.dmask, sc, R->tmp, s))) return st;
   if ((st = enq_residual64(R, R->tmp, R->res, sc, s))) return st;
   if ((st = enq_norm(R, R->res, R->aux + 0, s))) return st;
-  init_state_kernel<<<1, 1, 0, s>>>(R->st, R->tol, 1, nullptr, PCG_PAUSED);
+  init_state_kernel<<<1, 1, 0, s>>>(R->st, R->tol, 1, nullptr, PCG_PAUSED, 0);
   PFEM_COUNT_LAUNCH();
   R->phase = PH_NT_REF;
   return PFEM_OK;
@@ -423,7 +425,7 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
           break;
         }
       }
-      if (ps.done == PCG_CONVERGED || ps.done == PCG_MAXITER || stagnated) {
+      if (ps.done == PCG_CONVERGED || ps.done == PCG_MAXITER || ps.done == PCG_NEGCURV || stagnated) {
         R->inner_iters += ps.iter;
         R->repl += ps.replacements;
         R->t_ls = 1.0;

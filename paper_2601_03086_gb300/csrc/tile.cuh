@@ -362,9 +362,10 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
   CT* part = static_cast<CT*>(P.partial) + (size_t)region * P.n_partials * 4;
   int32_t* count = P.halo_count + (size_t)region * P.n_partials;
   const CT sc = A.out_scale ? CT(*A.out_scale) : CT(1);  // upstream factor (batched autograd)
+  const bool defer = A.defer_halo != 0;
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
-    int slot_i = 0;
-    if (l >= ncomp) slot_i = P.halo_rec[pbeg + l - ncomp].x;  // issued before the slot sums
+    int slot_i = pbeg + l - ncomp;  // deferred: tile order, no load on the way
+    if (l >= ncomp && !defer) slot_i = P.halo_rec[slot_i].x;  // issued before the slot sums
     const int b = soff[l], e = soff[l + 1];
     CT acc[4] = {CT(0), CT(0), CT(0), CT(0)};
     for (int k = b; k < e; ++k) {
@@ -381,7 +382,7 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
     // halo node: publish this tile's partial in the node's contiguous range
     st4(part + 4 * (size_t)slot_i, acc[0], acc[1], acc[2], CT(0));
   }
-  if (A.defer_halo) return;  // uniform: halo_finish_kernel completes the halo nodes
+  if (defer) return;  // uniform: halo_finish_kernel completes the halo nodes
   // Release once per tile: every partial of this tile is visible device-wide before any of
   // its tickets; the tile whose ticket completes a halo node's set (acquire fence after the
   // ticket) sums that node's partials in ascending tile order and writes the output.
@@ -620,6 +621,9 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
         if (pap == 0.0 || !isfinite(pap)) {
           st->alpha = 0.0;
           st->done = isfinite(pap) ? PCG_BREAKDOWN : PCG_NONFINITE;
+        } else if (pap < 0.0 && __ldcg(&st->truncate) != 0 && __ldcg(&st->iter) > 0) {
+          st->alpha = 0.0;  // truncated CG: keep the iterate reached with positive curvature
+          st->done = PCG_NEGCURV;
         } else {
           st->alpha = __ldcg(&st->rho) / pap;
         }
