@@ -411,19 +411,29 @@ def main():
     return 0
 
 
-def _committed_traffic(key):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
+TILE_SOURCES = ("kernels_tile.cu", "tile.cuh", "element.cuh", "pfem_internal.h")
+
+
+def tile_source_sha():
+    """Digest of the element-tile kernel sources (a committed ncu traffic figure is used only
+    while it still describes the compiled kernel)."""
     import hashlib
 
+    h = hashlib.sha256()
+    for name in TILE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2601_03086_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _committed_traffic(key):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_2601_03086_gb300", "csrc", "kernels_tile.cu")
     try:
         with open(path) as f:
             d = json.load(f)
-        with open(src, "rb") as f:
-            h = hashlib.sha256(f.read()).hexdigest()[:16]
         e = d.get(key)
-        if e and e.get("kernels_tile_sha") == h:
+        if e and e.get("tile_sources_sha") == tile_source_sha():
             return e["dram_bytes_per_launch"]
     except Exception:
         pass
