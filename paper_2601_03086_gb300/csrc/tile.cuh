@@ -171,7 +171,7 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
     CT t = a[0] * b[0];
 #pragma unroll
     for (int i = 1; i < DIM; ++i) t = fma(a[i], b[i], t);
-    return (double)t;
+    return t;
   };
   for (int f = threadIdx.x; f < nf; f += blockDim.x) {
     const ushort4 hd = shead[f];
@@ -201,29 +201,34 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
         }
       }
     }
-    // ring node state: edge from h_0, H x edge, field differences from h_0, raw v (PAP)
-    auto load_ring = [&](unsigned code, CT (&E)[3], CT (&Q)[3], CT (&du)[3], CT (&dv)[3], CT (&vr)[3]) {
+    // ring node records (x, u, v) fetched one step ahead of their use
+    struct Ring {
+      CT x[4], u[4], v[4];
+    };
+    auto fetch_ring = [&](unsigned code, Ring& g) {
       const int l = (int)(code & 1023u);
-      CT t[4];
-      ld4(sx + 4 * l, t);
+      ld4(sx + 4 * l, g.x);
+      if constexpr (NEED_GU) ld4(su + 4 * l, g.u);
+      if constexpr (NEED_GV) ld4(sv + 4 * l, g.v);
+    };
+    // ring node state: edge from h_0, H x edge, field differences from h_0, raw v (PAP)
+    auto derive_ring = [&](const Ring& g, CT (&E)[3], CT (&Q)[3], CT (&du)[3], CT (&dv)[3], CT (&vr)[3]) {
 #pragma unroll
-      for (int i = 0; i < 3; ++i) E[i] = t[i] - x0[i];
+      for (int i = 0; i < 3; ++i) E[i] = g.x[i] - x0[i];
       if constexpr (DIM == 3) {
         Q[0] = H[1] * E[2] - H[2] * E[1];
         Q[1] = H[2] * E[0] - H[0] * E[2];
         Q[2] = H[0] * E[1] - H[1] * E[0];
       }
       if constexpr (NEED_GU) {
-        ld4(su + 4 * l, t);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) du[i] = t[i] - u0[i];
+        for (int i = 0; i < 3; ++i) du[i] = g.u[i] - u0[i];
       }
       if constexpr (NEED_GV) {
-        ld4(sv + 4 * l, t);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-          dv[i] = t[i] - v0[i];
-          vr[i] = t[i];
+          dv[i] = g.v[i] - v0[i];
+          vr[i] = g.v[i];
         }
       }
     };
@@ -233,16 +238,30 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
     unsigned cc = hd.z;
     CT Ec[3], Qc[3] = {CT(0), CT(0), CT(0)}, duc[3] = {CT(0), CT(0), CT(0)}, dvc[3] = {CT(0), CT(0), CT(0)},
               vc[3] = {CT(0), CT(0), CT(0)};
-    load_ring(cc, Ec, Qc, duc, dvc, vc);
+    Ring gnext;
+    fetch_ring(cc, gnext);
+    derive_ring(gnext, Ec, Qc, duc, dvc, vc);
     int s = f;  // step record of the tile (step-major: step i of fan f at sum_{j<i} cnt_j + f)
+    unsigned cnext = 0;
+    M2 mnext{};
+    if (k > 0) {
+      cnext = scode[s];
+      mnext = smat[s];
+      fetch_ring(cnext, gnext);
+    }
+    CT e_fan = CT(0);  // PAP: this fan's share of v . A v
     for (int i = 0; i < k; ++i) {
-      const unsigned cn = scode[s];
-      const M2 m = smat[s];
-      const CT mu = m.x, lam = m.y;
-      s += scnt[i];
+      const unsigned cn = cnext;
+      const CT mu = mnext.x, lam = mnext.y;
       CT En[3], Qn[3] = {CT(0), CT(0), CT(0)}, dun[3] = {CT(0), CT(0), CT(0)}, dvn[3] = {CT(0), CT(0), CT(0)},
                 vn[3] = {CT(0), CT(0), CT(0)};
-      load_ring(cn, En, Qn, dun, dvn, vn);
+      derive_ring(gnext, En, Qn, dun, dvn, vn);
+      s += scnt[i];
+      if (i + 1 < k) {  // the next step's record and ring node, in flight during this simplex
+        cnext = scode[s];
+        mnext = smat[s];
+        fetch_ring(cnext, gnext);
+      }
       ElemGeo<DIM, CT> G;
       fan_geometry<DIM, CT>(H, Ec, En, Qc, Qn, G);
       // corner differences from h_0 of the simplex's fields
@@ -325,7 +344,7 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
           accc[j] += out[HS][j];
         }
         put(cc, accc);  // ring node i is complete: it touches simplices i - 1 and i only
-        if constexpr (PAP) e_acc += dot3(vc, accc);
+        if constexpr (PAP) e_fan += dot3(vc, accc);
 #pragma unroll
         for (int j = 0; j < DIM; ++j) accc[j] = out[HS + 1][j];
       }
@@ -345,8 +364,9 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
       if constexpr (DIM == 3) put(hd.y, acc1);
       if constexpr (PAP) {
         CT v0c[3] = {v0[0], v0[1], v0[2]};
-        e_acc += dot3(vc, accc) + dot3(v0c, acc0);
-        if constexpr (DIM == 3) e_acc += dot3(v1, acc1);
+        e_fan += dot3(vc, accc) + dot3(v0c, acc0);
+        if constexpr (DIM == 3) e_fan += dot3(v1, acc1);
+        e_acc += (double)e_fan;
       }
     }
   }

@@ -1,0 +1,45 @@
+"""Newton-Krylov on a zero-start Neo-Hookean bar whose lifted end layer is stretched by ~100 %
+(indefinite tangents near the grip): with enough load steps it matches the oracle; with too
+few, the truncated inner CG and the inner iteration cap keep the work bounded whatever the
+outcome."""
+
+import numpy as np
+import pytest
+
+import pfem_inputs as pi
+from oracle import fem, solve
+from tests.gpu_util import pfem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+INNER_CAP = 20000  # inner PCG iterations per tangent solve at most
+
+
+@pytest.fixture(scope="module")
+def bar():
+    reqs = pi.cfg5_requests(n_requests=8, seed=5, hi=200_000)
+    r = reqs[5]  # 24 x 6 x 6 hexes, 10 % stretch, zero start
+    assert r["kind"] == "neohookean" and tuple(r["dims"]) == (24, 6, 6)
+    return pi.request_problem(r)
+
+
+def test_five_load_steps_match_oracle(bar):
+    P = pfem()
+    m = fem.Mesh(bar)
+    u_ref, n_ref, _ = solve.solve_newton(m, tol=1e-8, n_load_steps=5, direct=True)
+    mesh = P.Mesh(bar)
+    u, info = P.pfem_solve_newton(mesh, tol=1e-8, n_load_steps=5)
+    assert info["status"] == 0
+    assert abs(info["newton_iterations"] - n_ref) <= 3, (info, n_ref)
+    assert rel_l2(u.cpu().numpy(), u_ref) <= 1e-6
+
+
+def test_two_load_steps_bounded_work(bar):
+    P = pfem()
+    mesh = P.Mesh(bar)
+    u, info = P.pfem_solve_newton(mesh, tol=1e-8, n_load_steps=2, raise_on_error=False)
+    assert info["iterations"] <= INNER_CAP * (info["newton_iterations"] + 1), info
+    if info["status"] == 0:
+        m = fem.Mesh(bar)
+        r = fem.residual(m, u.cpu().numpy(), 1.0)
+        assert np.isfinite(r).all()
