@@ -50,38 +50,6 @@ struct ElemGeo {
   CT det, rdet, s, kappa;
 };
 
-// X[a][i], a = 0..DIM (only the first DIM components are used)
-template <int DIM, typename CT>
-__device__ __forceinline__ void geometry(const CT (&X)[DIM + 1][4], ElemGeo<DIM, CT>& G) {
-  if constexpr (DIM == 3) {
-    CT d[3][3];  // d[a][i] = X_{a+1,i} - X_{0,i}
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) d[a][i] = X[a + 1][i] - X[0][i];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int b = (a + 1) % 3, e = (a + 2) % 3;  // c_a = d_b x d_e
-      G.c[a][0] = d[b][1] * d[e][2] - d[b][2] * d[e][1];
-      G.c[a][1] = d[b][2] * d[e][0] - d[b][0] * d[e][2];
-      G.c[a][2] = d[b][0] * d[e][1] - d[b][1] * d[e][0];
-    }
-    G.det = d[0][0] * G.c[0][0] + d[0][1] * G.c[0][1] + d[0][2] * G.c[0][2];
-  } else {
-    const CT d00 = X[1][0] - X[0][0], d01 = X[1][1] - X[0][1];  // d_1
-    const CT d10 = X[2][0] - X[0][0], d11 = X[2][1] - X[0][1];  // d_2
-    G.c[0][0] = d11;
-    G.c[0][1] = -d10;
-    G.c[1][0] = -d01;
-    G.c[1][1] = d00;
-    G.det = d00 * d11 - d01 * d10;
-  }
-  G.rdet = drcp<CT>(G.det);
-  const CT inv_fact = CT(1.0 / Factorial<DIM>::value);
-  G.kappa = G.rdet > CT(0) ? inv_fact : -inv_fact;
-  G.s = fabs(G.rdet) * inv_fact;
-}
-
 // Simplex i of a fan: corners (h_0, h_1, r_i, r_{i+1}) in 3-D, (h_0, r_i, r_{i+1}) in 2-D,
 // from the edges Ei = r_i - h_0, En = r_{i+1} - h_0 and (3-D) H = h_1 - h_0 with
 // Qj = H x Ej, each formed once per ring node: the adjugate rows are
@@ -125,35 +93,6 @@ __device__ __forceinline__ void grad_prime_d(const ElemGeo<DIM, CT>& G, const CT
       for (int a = 1; a < DIM; ++a) t = fma(dw[a][i], G.c[a][j], t);
       Gp[i][j] = t;
     }
-}
-
-// Unscaled gradient G' = sum_{a>=1} (w_a - w_0) (x) c_a  (grad w = G' / det)
-template <int DIM, typename CT>
-__device__ __forceinline__ void grad_prime(const ElemGeo<DIM, CT>& G, const CT (&w)[DIM + 1][3], CT (&Gp)[DIM][DIM]) {
-  CT dw[DIM][DIM];
-#pragma unroll
-  for (int a = 0; a < DIM; ++a)
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) dw[a][i] = w[a + 1][i] - w[0][i];
-#pragma unroll
-  for (int i = 0; i < DIM; ++i)
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) {
-      CT t = dw[0][i] * G.c[0][j];
-#pragma unroll
-      for (int a = 1; a < DIM; ++a) t = fma(dw[a][i], G.c[a][j], t);
-      Gp[i][j] = t;
-    }
-}
-
-// grad w = G' / det
-template <int DIM, typename CT>
-__device__ __forceinline__ void grad_of(const ElemGeo<DIM, CT>& G, const CT (&w)[DIM + 1][3], CT (&Gw)[DIM][DIM]) {
-  grad_prime<DIM, CT>(G, w, Gw);
-#pragma unroll
-  for (int i = 0; i < DIM; ++i)
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) Gw[i][j] *= G.rdet;
 }
 
 // out_{a+1} = T c_a, out_0 = -sum (T already carries the element's scale)

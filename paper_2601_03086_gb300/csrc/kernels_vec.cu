@@ -155,11 +155,6 @@ __global__ void axpy_kernel(int64_t n, double a, const double* x, double* y) {
     y[i] += a * x[i];
 }
 
-__global__ void scale_copy_kernel(int64_t n, double a, const double* x, double* y) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    y[i] = a * x[i];
-}
-
 static inline int vec_grid(int64_t n) {
   int64_t g = (n + 255) / 256;
   if (g > 152 * 8) g = 152 * 8;
@@ -221,12 +216,6 @@ pfem_status vk_norm2(int64_t n, const double* v, double* out, double* partials, 
 
 pfem_status vk_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
   axpy_kernel<<<vec_grid(n), 256, 0, s>>>(n, a, x, y); PFEM_COUNT_LAUNCH();
-  PFEM_CUDA(cudaGetLastError());
-  return PFEM_OK;
-}
-
-pfem_status vk_scale_copy(int64_t n, double a, const double* x, double* y, cudaStream_t s) {
-  scale_copy_kernel<<<vec_grid(n), 256, 0, s>>>(n, a, x, y); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }

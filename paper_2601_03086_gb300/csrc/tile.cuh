@@ -1,17 +1,20 @@
-// Element-tile kernel: one CTA per tile, shared-memory staging of the tile's nodes, one
-// thread per element (strided), per-incidence slots, fixed-order node sums, and halo nodes
-// finished in-kernel by the last tile to publish its partial.
+// Element-tile kernel: one CTA per tile, shared-memory staging of the tile's nodes and
+// element records, one thread per fan (a chain of simplices around a shared hinge, see
+// pfem_internal.h), per-(fan, node) slots, fixed-order node sums, and halo nodes completed
+// either in-kernel by the last tile to publish a partial (integer ticket per halo node) or
+// by a separate pass over tile-ordered partials (large single-mesh launches).
 //
-// Passes of one tile CTA (every requested output op runs its own element and node pass;
+// Passes of one tile CTA (every requested output op runs its own fan and node pass;
 // element quantities are recomputed, never stored):
-//   stage : tile node coordinates (tile-relative, FP32 or FP64) + u and/or v gathered by id
-//   elem  : per element geometry, kinematics, stress / stress derivative, V * T dN_a into
-//           slot (node, rank); optional V * Psi accumulated per thread
+//   stage : step records and fan heads, tile node coordinates (tile-relative, FP32 or FP64)
+//           and u and/or v gathered by node id
+//   fans  : thread f walks fan f's ring: per simplex geometry, kinematics, stress / stress
+//           derivative and V * T dN_a; a ring node's two contributions are summed in
+//           registers and written once to its slot; optional V * Psi per thread
 //   node  : each tile node sums its slots in rank order; a complete node writes its output;
-//           a halo node publishes a partial, and the tile whose partial completes the set
-//           (integer ticket per halo node) sums all partials of that node in ascending tile
-//           order and writes the output. The summation order never depends on timing, so the
-//           result is bitwise reproducible; the ticket is reset by that last tile.
+//           a halo node publishes a partial, and the node is finished by summing all its
+//           partials in ascending tile order. The summation order never depends on timing,
+//           so the result is bitwise reproducible.
 //
 // Output conventions (Dirichlet DOFs eliminated): tangent y = v on prescribed DOFs and v is
 // read as 0 there; residual r = 0 on prescribed DOFs; diagonal d = 1 on prescribed DOFs.
@@ -129,17 +132,6 @@ __device__ __forceinline__ void final_write(const DevPlan& P, const OpArgs& A, i
       static_cast<VT*>(A.d)[k] = fixed ? VT(1) : VT(acc[i]);
     }
   }
-}
-
-// v_e . y_e over the corners of one element (the element's share of v . A v)
-template <int DIM, typename CT>
-__device__ __forceinline__ double corner_dot(const CT (&w)[DIM + 1][3], const CT (&out)[DIM + 1][DIM]) {
-  CT s = CT(0);
-#pragma unroll
-  for (int a = 0; a <= DIM; ++a)
-#pragma unroll
-    for (int i = 0; i < DIM; ++i) s = fma(w[a][i], out[a][i], s);
-  return (double)s;
 }
 
 // One fan pass for output OUT (or energy only when OUT < 0): thread f walks the ring of fan
