@@ -490,7 +490,7 @@ def _batch_loss(P, pi, torch, np):
             "tets_per_s": n_tets * 1e3 / ms, "ops": "energy + gradient + Hessian-vector, FP32 elements"}
 
 
-def _serving(P, pi, torch, np, n_req=200, rate_factor=20.0, hi=50_000):
+def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
     """Scaled sample of the serving workload: the first n_req records of the seeded request
     stream (Poisson arrivals, 70% linear cubes / 30% Neo-Hookean bars at 10% stretch, 50%
     warm started), mesh sizes log-uniform in [2k, hi] tets (the full stream goes to 2M), tol
@@ -557,7 +557,7 @@ def _serving(P, pi, torch, np, n_req=200, rate_factor=20.0, hi=50_000):
     rate = rate_factor * out["plain_loop"]["solves_per_s"]
     out["arrival_rate_per_s"] = rate
     arrive = np.cumsum([r["gap"] for r in reqs]) / rate
-    server = P.Server(120 << 30, max_slots=64)
+    server = P.Server(120 << 30, max_slots=128)
     tickets, t_sub, done = [], [], {}
     t0 = time.perf_counter()
     i = 0

@@ -99,7 +99,7 @@ size_t mesh_arena_bytes(const HostPlan& hp) {
 }
 
 pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, const pfem_mesh_desc* desc,
-                        cudaStream_t stream, pfem_mesh_t* out) {
+                        cudaStream_t stream, pfem_mesh_t* out, cudaMemPool_t pool) {
   pfem_status st = PFEM_OK;
   void* cuda_stream = stream;
   const int dim = hp.dim;
@@ -151,25 +151,35 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   }
   m->stream = static_cast<cudaStream_t>(cuda_stream);
   cudaGetDevice(&m->device);
-  cudaError_t ce = cudaMalloc(&m->arena, ab.off);
+  m->pooled = pool != nullptr;
+  cudaError_t ce = m->pooled ? cudaMallocFromPoolAsync(&m->arena, ab.off, pool, m->stream) : cudaMalloc(&m->arena, ab.off);
   if (ce != cudaSuccess) {
     delete m;
-    return cuda_fail(ce, "cudaMalloc(mesh arena)");
+    return cuda_fail(ce, "device allocation (mesh arena)");
   }
   m->arena_bytes = ab.off;
-  ce = cudaMallocHost(&m->host_out, 8 * sizeof(double) + 4 * sizeof(int32_t));
-  if (ce != cudaSuccess) {
-    cudaFree(m->arena);
-    delete m;
-    return cuda_fail(ce, "cudaMallocHost");
+  auto release = [m]() {
+    if (m->pooled) {
+      cudaFreeAsync(m->arena, m->stream);
+    } else {
+      cudaFree(m->arena);
+    }
+    if (m->host_out) cudaFreeHost(m->host_out);
+  };
+  if (!m->pooled) {  // pinned scratch of the synchronous host-result calls
+    ce = cudaMallocHost(&m->host_out, 8 * sizeof(double) + 4 * sizeof(int32_t));
+    if (ce != cudaSuccess) {
+      cudaFree(m->arena);
+      delete m;
+      return cuda_fail(ce, "cudaMallocHost");
+    }
+    m->host_int = reinterpret_cast<int32_t*>(m->host_out + 8);
   }
-  m->host_int = reinterpret_cast<int32_t*>(m->host_out + 8);
   char* base = static_cast<char*>(m->arena);
   cudaStream_t s = m->stream;
   auto fail = [&](pfem_status e) {
     cudaStreamSynchronize(s);
-    cudaFree(m->arena);
-    cudaFreeHost(m->host_out);
+    release();
     delete m;
     return e;
   };
@@ -280,6 +290,11 @@ pfem_status pfem_plan_check(const pfem_mesh_desc* desc, pfem_mesh_stats* out) {
 
 void pfem_mesh_destroy(pfem_mesh_t m) {
   if (!m) return;
+  if (m->pooled) {  // serving: returned to the pool in stream order, no device synchronisation
+    cudaFreeAsync(m->arena, m->stream);
+    delete m;
+    return;
+  }
   cudaStreamSynchronize(m->stream);
   solver_release(m);
   cudaFree(m->arena);

@@ -113,8 +113,10 @@ pfem_status build_plan(const pfem_mesh_desc* d, HostPlan* plan, std::vector<doub
 
 // Device bytes of a mesh built from hp, and the upload that builds it (capi.cu).
 size_t mesh_arena_bytes(const HostPlan& hp);
+// pool != nullptr (serving): the arena comes from that stream-ordered memory pool on `stream`
+// and is returned to it without a device synchronisation; no pinned host scratch.
 pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, const pfem_mesh_desc* desc,
-                        cudaStream_t stream, pfem_mesh_t* out);
+                        cudaStream_t stream, pfem_mesh_t* out, cudaMemPool_t pool = nullptr);
 
 // Default elements per tile for a mesh of n_elems elements.
 int default_tile_elems(int64_t n_elems);
@@ -327,6 +329,7 @@ struct pfem_mesh_s {
   int device = 0;
   double load_scale = 1.0;
   void* arena = nullptr;     // single device allocation holding every plan array
+  bool pooled = false;       // arena from a stream-ordered pool (serving): freed on `stream`
   size_t arena_bytes = 0;
   // small device scratch for reductions
   double* red_partials = nullptr;   // kReduceBlocks * 4 doubles

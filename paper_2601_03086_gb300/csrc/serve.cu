@@ -139,6 +139,7 @@ struct pfem_server_s {
   int max_slots = 1;
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;    // stream-ordered allocations of resident solves
   std::mutex mu;
   std::condition_variable cv_work, cv_plan, cv_done;
   std::deque<Request*> queue;      // submitted, in arrival order (planned or not)
@@ -187,7 +188,7 @@ size_t request_bytes(const HostPlan& hp) {
 }
 
 pfem_status admit(pfem_server_s* S, Request* R) {
-  pfem_status st = mesh_upload(R->plan, R->fext, &R->desc, S->stream, &R->mesh);
+  pfem_status st = mesh_upload(R->plan, R->fext, &R->desc, S->stream, &R->mesh, S->pool);
   if (st) return st;
   R->n = R->mesh->n_dofs;
   R->nublk = serve_update_blocks(R->n);
@@ -195,8 +196,8 @@ pfem_status admit(pfem_server_s* S, Request* R) {
   const size_t tb = ((size_t)std::max(R->mesh->plan.n_tiles, 1) * 8 + 255) & ~size_t(255);
   const size_t ub = ((size_t)R->nublk * 16 + 255) & ~size_t(255);
   const size_t bytes = 10 * vb + tb + ub + 1024;
-  cudaError_t e = cudaMalloc(&R->block, bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(serving workspace)");
+  cudaError_t e = cudaMallocFromPoolAsync(&R->block, bytes, S->pool, S->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "device allocation (serving workspace)");
   char* b = static_cast<char*>(R->block);
   double** v[10] = {&R->x, &R->r, &R->p0, &R->p1, &R->q, &R->dinv, &R->res, &R->u, &R->rn, &R->tmp};
   for (int i = 0; i < 10; ++i) *v[i] = reinterpret_cast<double*>(b + i * vb);
@@ -335,7 +336,7 @@ void finish(pfem_server_s* S, Request* R, pfem_status status) {
   R->status = status;
   R->info.status = status;
   R->t_done = now_s();
-  if (R->block) cudaFree(R->block);
+  if (R->block) cudaFreeAsync(R->block, S->stream);  // stream-ordered: no device synchronisation
   R->block = nullptr;
   if (R->mesh) pfem_mesh_destroy(R->mesh);
   R->mesh = nullptr;
@@ -663,6 +664,23 @@ pfem_status pfem_serve_create(size_t hbm_budget_bytes, int32_t max_slots, pfem_s
     delete S;
     return cuda_fail(e, "cudaStreamCreate");
   }
+  // resident solves allocate and free through a pool that keeps its memory (up to the
+  // admission budget) instead of synchronising the device on every admission and release
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = S->device;
+  e = cudaMemPoolCreate(&S->pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t keep = (uint64_t)hbm_budget_bytes;
+    e = cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  if (e != cudaSuccess) {
+    if (S->pool) cudaMemPoolDestroy(S->pool);
+    cudaStreamDestroy(S->stream);
+    delete S;
+    return cuda_fail(e, "memory pool");
+  }
   unsigned hc = std::thread::hardware_concurrency();
   const int np = (int)std::max(1u, std::min(8u, hc > 2 ? hc / 2 : 1u));
   for (int i = 0; i < np; ++i) S->planners.emplace_back(plan_worker, S);
@@ -792,10 +810,11 @@ void pfem_serve_destroy(pfem_server_t S) {
   // requests that were never admitted or polled
   for (auto& kv : S->tickets) {
     Request* R = kv.second;
-    if (R->block) cudaFree(R->block);
+    if (R->block) cudaFreeAsync(R->block, S->stream);
     if (R->mesh) pfem_mesh_destroy(R->mesh);
     delete R;
   }
+  cudaStreamSynchronize(S->stream);  // pooled memory returned before the pool goes
   cudaFree(S->d_reqs);
   cudaFree(S->d_btile);
   cudaFree(S->d_ublk);
@@ -804,6 +823,7 @@ void pfem_serve_destroy(pfem_server_t S) {
   cudaFree(S->d_invp);
   cudaFree(S->d_slots);
   if (S->h_slots) cudaFreeHost(S->h_slots);
+  if (S->pool) cudaMemPoolDestroy(S->pool);
   cudaStreamDestroy(S->stream);
   delete S;
 }
