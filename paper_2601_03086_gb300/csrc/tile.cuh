@@ -471,6 +471,27 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
     int* sinfo = reinterpret_cast<int*>(smem + L.info);
     const VT* u = static_cast<const VT*>(A.u);
     const VT* v = static_cast<const VT*>(A.v);
+    // node records of this thread's first round (two nodes per thread and round), issued
+    // before the step records so that their latency and the step loads overlap
+    float4 rf[2];
+    int so[2] = {0, 0};
+    CT xc[2][3];
+    auto load_records = [&](int l0) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int l = l0 + q * (int)blockDim.x;
+        if (l >= nl) continue;
+        rf[q] = P.lnode_f[lbeg + l];
+        so[q] = (int)P.slot_off[lbeg + l];
+        if constexpr (sizeof(CT) == 4) {
+          xc[q][0] = rf[q].x, xc[q][1] = rf[q].y, xc[q][2] = rf[q].z;
+        } else {
+          const PfemDouble4 rd = P.lnode_d[lbeg + l];
+          xc[q][0] = rd.x, xc[q][1] = rd.y, xc[q][2] = rd.z;
+        }
+      }
+    };
+    if ((int)threadIdx.x < nl) load_records(threadIdx.x);
     {  // fan heads and step records (coalesced; read from shared memory by the fans)
       using M2 = typename std::conditional<sizeof(CT) == 4, float2, double2>::type;
       const M2* gmat = reinterpret_cast<const M2*>(sizeof(CT) == 4 ? static_cast<const void*>(P.step_mat_f)
@@ -500,24 +521,11 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
       }
       for (int j = threadIdx.x; j < nf; j += blockDim.x) shead[j] = P.fan_head[fbeg + j];
     }
-    // nodes, two per thread and round: records first, then the gathers their ids select
+    // nodes, two per thread and round: records (the first round's are in flight already),
+    // then the gathers their ids select
     for (int l0 = threadIdx.x; l0 < nl; l0 += 2 * blockDim.x) {
       const int ls[2] = {l0, l0 + (int)blockDim.x};
-      float4 rf[2];
-      int so[2] = {0, 0};
-      CT xc[2][3];
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        if (ls[q] >= nl) continue;
-        rf[q] = P.lnode_f[lbeg + ls[q]];
-        so[q] = (int)P.slot_off[lbeg + ls[q]];
-        if constexpr (sizeof(CT) == 4) {
-          xc[q][0] = rf[q].x, xc[q][1] = rf[q].y, xc[q][2] = rf[q].z;
-        } else {
-          const PfemDouble4 rd = P.lnode_d[lbeg + ls[q]];
-          xc[q][0] = rd.x, xc[q][1] = rd.y, xc[q][2] = rd.z;
-        }
-      }
+      if (l0 != (int)threadIdx.x) load_records(l0);
       CT wu[2][3], wv[2][3];
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
