@@ -1,8 +1,9 @@
 """Small drivers of the library's kernels for profilers (ncu) and quick timing.
 
     python -m paper_2601_03086_gb300.probe apply --n 160 --reps 3 [--vec f64] [--kind nh]
-        tangent apply on the n^3 x 6 Kuhn cube (FP32 element arithmetic; f64 = FP64
-        vectors with FP32 arithmetic, the PCG configuration)
+            [--op residual]
+        tangent apply (or residual) on the n^3 x 6 Kuhn cube (FP32 element arithmetic;
+        f64 = FP64 vectors with FP32 arithmetic, the PCG configuration)
     python -m paper_2601_03086_gb300.probe solve --n 40 --max-iter 40 [--mode plain]
         Jacobi-PCG on the n^3 cube (the benchmark workload at n = 40); --mode persistent
         (default), graph, or plain (one kernel at a time, so a profiler can attribute time
@@ -29,6 +30,7 @@ def main(argv=None):
     ap.add_argument("--kind", choices=["linear", "nh"], default="linear")
     ap.add_argument("--max-iter", type=int, default=100000)
     ap.add_argument("--mode", choices=["persistent", "plain", "graph"], default="persistent")
+    ap.add_argument("--op", choices=["tangent", "residual"], default="tangent")
     a = ap.parse_args(argv)
 
     import torch
@@ -51,13 +53,23 @@ def main(argv=None):
         u = 0.01 * torch.randn_like(v) if a.kind == "nh" else None
         y = torch.empty_like(v)
         arith = "f32" if a.vec == "f64" else None
-        P.pfem_tangent_apply(mesh, u, v, y, arith=arith)
+        if a.op == "residual":
+            u = 0.01 * torch.randn_like(v)
+
+        def op():
+            if a.op == "tangent":
+                P.pfem_tangent_apply(mesh, u, v, y, arith=arith)
+            else:
+                P.pfem_residual(mesh, u, y, arith=arith)
+
+        op()
         ev[0].record()
         for _ in range(a.reps):
-            P.pfem_tangent_apply(mesh, u, v, y, arith=arith)
+            op()
         ev[1].record()
         ev[1].synchronize()
         out["apply_us"] = ev[0].elapsed_time(ev[1]) * 1e3 / a.reps
+        out["op"] = a.op
     else:
         P.pfem_set_solver_mode({"persistent": 0, "plain": 1, "graph": 2}[a.mode])
         P.pfem_solve_linear(mesh, tol=1e-8, max_iter=a.max_iter, raise_on_error=False)
