@@ -85,7 +85,10 @@ __global__ void __launch_bounds__(kReduceThreads)
                       cudaGraphConditionalHandle cond, int set_cond) {
   __shared__ double scratch[16];
   if (st->done != 0 || st->repl != 0) {  // nothing to do (uniform: written by earlier kernels)
-    if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) cudaGraphSetConditional(cond, 0u);
+    if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) {
+      st->bodies += 1;
+      cudaGraphSetConditional(cond, 0u);
+    }
     return;
   }
   const double alpha = st->alpha;
@@ -94,7 +97,10 @@ __global__ void __launch_bounds__(kReduceThreads)
   pcg_update_range<4>(n, x, r, p, q, dinv, alpha, blockIdx.x, v);  // launched as kReduceBlocks x kReduceThreads
   if (grid_sum<2>(v, partials, counter, scratch) && threadIdx.x == 0) {
     pcg_finish_update(st, v[0], v[1]);
-    if (set_cond) cudaGraphSetConditional(cond, (st->done == 0 && st->repl == 0) ? 1u : 0u);
+    if (set_cond) {
+      st->bodies += 1;
+      cudaGraphSetConditional(cond, (st->done == 0 && st->repl == 0) ? 1u : 0u);
+    }
   }
 }
 

@@ -200,6 +200,7 @@ struct PcgState {
   int repl;               // 1 = stop the device loop for an FP64 residual replacement
   int replacements;
   int truncate;           // 1: stop at negative curvature after the first iteration (Newton inner solves)
+  int bodies;             // replays of the graph loop body (counted by its last kernel)
 };
 
 // Extra inputs of the PCG-fused tangent apply (OP_PCG): the search direction is formed on

@@ -130,6 +130,10 @@ static pfem_status pcg_body(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_
                    s);
 }
 
+// PCG iterations per replay of the graph's while-loop body (fewer conditional-node
+// evaluations per iteration; the iterates do not depend on it).
+constexpr int kGraphUnroll = 8;
+
 static pfem_status build_graph(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   PFEM_CUDA(cudaGraphCreate(&g, 0));
@@ -163,7 +167,11 @@ static pfem_status build_graph(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool u
   e = cudaStreamBeginCaptureToGraph(w->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
   if (e != cudaSuccess) return fail(e);
   const int64_t before = g_kernel_launches;
-  const pfem_status st = pcg_body(m, w, ct, use_u, w->cap, h, 1);
+  // kGraphUnroll iterations per replay of the body; the kernels of an iteration after the
+  // state stops return at once, and only the body's last update sets the condition
+  pfem_status st = PFEM_OK;
+  for (int j = 0; j < kGraphUnroll && st == PFEM_OK; ++j)
+    st = pcg_body(m, w, ct, use_u, w->cap, h, j == kGraphUnroll - 1 ? 1 : 0);
   w->body_kernels[ct == PFEM_F64][use_u ? 1 : 0] = g_kernel_launches - before;
   g_kernel_launches = before;  // captured, not run: replays are counted per launch
   e = cudaStreamEndCapture(w->cap, &body);
@@ -218,13 +226,13 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
   bool replaced = true;  // the start is an FP64 true residual too
   double prev_true = -1.0;
   int stalls = 0;
-  int pending_iter0 = -1;  // iteration count before the last graph launch
+  int pending_bodies0 = -1;  // body replays counted before the last graph launch
   int64_t pending_body = 0;
   for (;;) {
     if ((st = read_state(m, w))) return st;
-    if (pending_iter0 >= 0) {  // a graph replay ran (iterations x body) + the pre-node
-      g_kernel_launches += (int64_t)(w->hst->iter - pending_iter0) * pending_body + 1;
-      pending_iter0 = -1;
+    if (pending_bodies0 >= 0) {  // a graph launch ran (body replays x body) + the pre-node
+      g_kernel_launches += (int64_t)(w->hst->bodies - pending_bodies0) * pending_body + 1;
+      pending_bodies0 = -1;
     }
     if (replaced) {
       replaced = false;
@@ -265,7 +273,7 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
       *ex = nullptr;
     }
     if (g_solver_mode != 1 && !w->graph_failed && *ex) {
-      pending_iter0 = w->hst->iter;
+      pending_bodies0 = w->hst->bodies;
       pending_body = w->body_kernels[ct == PFEM_F64][ui];
       PFEM_CUDA(cudaGraphLaunch(*ex, s));
     } else {
