@@ -56,45 +56,77 @@ __global__ void invert_diag_kernel(int64_t n, const T* d, double* dinv) {
   }
 }
 
-// alpha = rho / (p . q)
-__global__ void __launch_bounds__(kReduceThreads)
-    pcg_alpha_kernel(int64_t n, const double* p, const double* q, PcgState* st, double* partials,
-                     unsigned int* counter) {
-  __shared__ double scratch[8];
-  double v[1] = {0.0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    v[0] += p[i] * q[i];
-  if (grid_sum<1>(v, partials, counter, scratch) && threadIdx.x == 0) {
-    // Negative curvature (an indefinite tangent far from equilibrium) does not stop the
-    // iteration, as in plain CG; only p.q = 0 or a non-finite value does.
-    const double pq = v[0];
-    if (pq == 0.0 || !isfinite(pq)) {
-      st->alpha = 0.0;
-      st->done = isfinite(pq) ? PCG_BREAKDOWN : PCG_NONFINITE;
-    } else {
-      st->alpha = st->rho / pq;
-    }
-  }
-}
-
-// x += alpha p; r -= alpha q; (r.z, r.r) with z = dinv r; flags and beta in the last block.
-// p is this iteration's direction, p_buf[(iter + 1) & 1] (written by the fused apply).
+// alpha = rho / p.Ap from the fused apply's tile sums (every block forms it, in the same
+// order: same bits), then x += alpha p; r -= alpha q; (r.z, r.r) with z = dinv r; flags and
+// beta in the last block. p is this iteration's direction, p_buf[(iter + 1) & 1]. The first
+// chunk's vector loads are issued before the tile sum, so the two latencies overlap.
 __global__ void __launch_bounds__(kReduceThreads)
     pcg_update_kernel(int64_t n, double* x, double* r, const double* p0, const double* p1, const double* q,
-                      const double* dinv, PcgState* st, double* partials, unsigned int* counter,
-                      cudaGraphConditionalHandle cond, int set_cond) {
+                      const double* dinv, PcgState* st, const double* tile_part, int n_tiles, double* partials,
+                      unsigned int* counter, cudaGraphConditionalHandle cond, int set_cond) {
   __shared__ double scratch[16];
-  if (st->done != 0 || st->repl != 0) {  // nothing to do (uniform: written by earlier kernels)
+  __shared__ double s_alpha;
+  __shared__ int s_stop;
+  // every state field this kernel reads, loaded before the branch (one round trip); rho is
+  // rewritten only by the last block, after every block has read it
+  const int done = st->done, repl = st->repl, it = st->iter, trunc = st->truncate;
+  const double rho = st->rho;
+  if (done != 0 || repl != 0) {  // nothing to do (uniform: written by earlier kernels)
     if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) {
       st->bodies += 1;
       cudaGraphSetConditional(cond, 0u);
     }
     return;
   }
-  const double alpha = st->alpha;
-  const double* p = ((st->iter + 1) & 1) ? p1 : p0;
+  const double* p = ((it + 1) & 1) ? p1 : p0;
+  constexpr int U = 4;
+  const int64_t S = (int64_t)kReduceBlocks * kReduceThreads;
+  const int64_t i0 = (int64_t)blockIdx.x * kReduceThreads + threadIdx.x;
+  double pp[U], qq[U], rr[U], dd[U], xx[U];
+#pragma unroll
+  for (int j = 0; j < U; ++j) {
+    const int64_t k = i0 + j * S;
+    if (k < n) {
+      pp[j] = __ldcg(p + k);
+      qq[j] = __ldcg(q + k);
+      rr[j] = __ldcg(r + k);
+      dd[j] = dinv[k];
+      xx[j] = x[k];
+    }
+  }
+  const double pap = pcg_tile_total(tile_part, n_tiles, scratch);
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    s_stop = pcg_alpha(pap, rho, trunc, it, &a);
+    s_alpha = a;
+    if (blockIdx.x == 0) {  // for the host; nothing in this launch reads it back
+      st->alpha = a;
+      if (s_stop) {
+        st->done = s_stop;
+        if (set_cond) {
+          st->bodies += 1;
+          cudaGraphSetConditional(cond, 0u);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (s_stop) return;  // uniform: every block formed the same p.Ap
+  const double alpha = s_alpha;
   double v[2] = {0.0, 0.0};
-  pcg_update_range<4>(n, x, r, p, q, dinv, alpha, blockIdx.x, v);  // launched as kReduceBlocks x kReduceThreads
+#pragma unroll
+  for (int j = 0; j < U; ++j) {  // same arithmetic and order as pcg_update_range
+    const int64_t k = i0 + j * S;
+    if (k < n) {
+      x[k] = xx[j] + alpha * pp[j];
+      const double ri = rr[j] - alpha * qq[j];
+      r[k] = ri;
+      v[0] += ri * (dd[j] * ri);
+      v[1] += ri * ri;
+    }
+  }
+  if (i0 + U * S < n)  // the rest (meshes of more than U x 296 x 256 DOFs)
+    pcg_update_range_from<U>(n, x, r, p, q, dinv, alpha, i0 + U * S, v);
   if (grid_sum<2>(v, partials, counter, scratch) && threadIdx.x == 0) {
     pcg_finish_update(st, v[0], v[1]);
     if (set_cond) {
@@ -102,14 +134,6 @@ __global__ void __launch_bounds__(kReduceThreads)
       cudaGraphSetConditional(cond, (st->done == 0 && st->repl == 0) ? 1u : 0u);
     }
   }
-}
-
-// p = dinv r + beta p (skipped while a replacement is pending or after termination)
-__global__ void pcg_direction_kernel(int64_t n, const double* r, const double* dinv, double* p, const PcgState* st) {
-  if (st->done != 0 || st->repl != 0) return;
-  const double beta = st->beta;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = dinv[i] * r[i] + beta * p[i];
 }
 
 // Residual replacement / (re)start: r = -res (res = P (f_int(x) - f), FP64 operator),
@@ -182,26 +206,12 @@ pfem_status vk_invert_diag(int64_t n, const void* d, pfem_dtype dt, double* dinv
   return PFEM_OK;
 }
 
-pfem_status vk_alpha(int64_t n, const double* p, const double* q, PcgState* st, double* partials,
-                     unsigned int* counter, cudaStream_t s) {
-  pcg_alpha_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, p, q, st, partials, counter); PFEM_COUNT_LAUNCH();
-  PFEM_CUDA(cudaGetLastError());
-  return PFEM_OK;
-}
-
 pfem_status vk_update(int64_t n, double* x, double* r, const double* p0, const double* p1, const double* q,
-                      const double* dinv, PcgState* st, double* partials, unsigned int* counter,
-                      cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s) {
-  pcg_update_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, x, r, p0, p1, q, dinv, st, partials, counter, cond,
-                                                            set_cond);
+                      const double* dinv, PcgState* st, const double* tile_part, int n_tiles, double* partials,
+                      unsigned int* counter, cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s) {
+  pcg_update_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, x, r, p0, p1, q, dinv, st, tile_part, n_tiles,
+                                                            partials, counter, cond, set_cond);
   PFEM_COUNT_LAUNCH();
-  PFEM_CUDA(cudaGetLastError());
-  return PFEM_OK;
-}
-
-pfem_status vk_direction(int64_t n, const double* r, const double* dinv, double* p, const PcgState* st,
-                         cudaStream_t s) {
-  pcg_direction_kernel<<<vec_grid(n), 256, 0, s>>>(n, r, dinv, p, st); PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }

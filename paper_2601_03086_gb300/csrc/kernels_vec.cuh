@@ -10,13 +10,9 @@ namespace pfem {
 pfem_status vk_lift(int64_t n, const double* u0, const double* values, const uint8_t* mask, double s, double* x,
                     cudaStream_t st);
 pfem_status vk_invert_diag(int64_t n, const void* d, pfem_dtype dt, double* dinv, cudaStream_t st);
-pfem_status vk_alpha(int64_t n, const double* p, const double* q, PcgState* st, double* partials,
-                     unsigned int* counter, cudaStream_t s);
 pfem_status vk_update(int64_t n, double* x, double* r, const double* p0, const double* p1, const double* q,
-                      const double* dinv, PcgState* st, double* partials, unsigned int* counter,
-                      cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s);
-pfem_status vk_direction(int64_t n, const double* r, const double* dinv, double* p, const PcgState* st,
-                         cudaStream_t s);
+                      const double* dinv, PcgState* st, const double* tile_part, int n_tiles, double* partials,
+                      unsigned int* counter, cudaGraphConditionalHandle cond, int set_cond, cudaStream_t s);
 pfem_status vk_replace(int64_t n, const double* res, double* r, const double* dinv, PcgState* st, int restart,
                        double* partials, unsigned int* counter, cudaStream_t s);
 pfem_status vk_norm2(int64_t n, const double* v, double* out, double* partials, unsigned int* counter,

@@ -13,23 +13,54 @@ namespace pfem {
 // The state is read through L2 only: inside a persistent launch another CTA may have
 // written it since this one last looked.
 __device__ __forceinline__ void pcg_finish_update(PcgState* st, double rz, double rr) {
+  // every field this needs, loaded before the first store (one round trip)
   const int iter = __ldcg(&st->iter) + 1;
   const int done = __ldcg(&st->done);
+  const int max_iter = __ldcg(&st->max_iter);
+  const double ref = __ldcg(&st->ref), tol = __ldcg(&st->tol), thr = __ldcg(&st->repl_threshold);
+  const double rho = __ldcg(&st->rho);
   st->iter = iter;
-  const double rel = sqrt(rr) / __ldcg(&st->ref);
+  const double rel = sqrt(rr) / ref;
   st->rel = rel;
   if (!isfinite(rz) || !isfinite(rr)) {
     if (done == 0) st->done = PCG_NONFINITE;
   } else if (done == 0) {
-    if (rel < __ldcg(&st->tol) || rel < __ldcg(&st->repl_threshold)) {
+    if (rel < tol || rel < thr) {
       st->repl = 1;  // the host verifies / replaces with the FP64 true residual
-    } else if (iter >= __ldcg(&st->max_iter)) {
+    } else if (iter >= max_iter) {
       st->done = PCG_MAXITER;
     } else {
-      st->beta = rz / __ldcg(&st->rho);
+      st->beta = rz / rho;
       st->rho = rz;
     }
   }
+}
+
+// p . A p from the per-tile sums, in one fixed order (thread t sums tiles t, t + 256, ...;
+// warp butterflies; warps in index order): every block that calls it, and the last tile of
+// the fused apply, get the same bits. Valid in thread 0; needs 256 threads and red[8].
+__device__ __forceinline__ double pcg_tile_total(const double* tile_part, int n_tiles, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n_tiles; i += blockDim.x) s += __ldcg(tile_part + i);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  double pap = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pap += red[w];
+  return pap;
+}
+
+// alpha from p . A p, or the reason to stop: p.Ap = 0 or non-finite ends the solve; negative
+// curvature ends a truncated (Newton inner) solve after its first iteration, and does not
+// stop plain CG. Returns 0 (go on, *alpha set) or a PCG_* code.
+__device__ __forceinline__ int pcg_alpha(double pap, double rho, int truncate, int iter, double* alpha) {
+  if (pap == 0.0 || !isfinite(pap)) return isfinite(pap) ? PCG_BREAKDOWN : PCG_NONFINITE;
+  if (pap < 0.0 && truncate != 0 && iter > 0) return PCG_NEGCURV;
+  *alpha = rho / pap;
+  return 0;
 }
 
 // The vector part of the update for the DOFs of reduction block vb (of kReduceBlocks x
@@ -39,10 +70,11 @@ __device__ __forceinline__ void pcg_finish_update(PcgState* st, double rz, doubl
 // of the plain loop (any U gives the same bits). r, p, q go through L2 only (other CTAs of a
 // persistent launch write them).
 template <int U>
-__device__ __forceinline__ void pcg_update_range(int64_t n, double* x, double* r, const double* p, const double* q,
-                                                 const double* dinv, double alpha, int vb, double (&v)[2]) {
+__device__ __forceinline__ void pcg_update_range_from(int64_t n, double* x, double* r, const double* p,
+                                                      const double* q, const double* dinv, double alpha, int64_t i0,
+                                                      double (&v)[2]) {
   const int64_t S = (int64_t)kReduceBlocks * kReduceThreads;
-  for (int64_t i = (int64_t)vb * kReduceThreads + threadIdx.x; i < n; i += U * S) {
+  for (int64_t i = i0; i < n; i += U * S) {
     double pp[U], qq[U], rr[U], dd[U], xx[U];
 #pragma unroll
     for (int j = 0; j < U; ++j) {
@@ -67,6 +99,12 @@ __device__ __forceinline__ void pcg_update_range(int64_t n, double* x, double* r
       }
     }
   }
+}
+
+template <int U>
+__device__ __forceinline__ void pcg_update_range(int64_t n, double* x, double* r, const double* p, const double* q,
+                                                 const double* dinv, double alpha, int vb, double (&v)[2]) {
+  pcg_update_range_from<U>(n, x, r, p, q, dinv, alpha, (int64_t)vb * kReduceThreads + threadIdx.x, v);
 }
 
 }  // namespace pfem

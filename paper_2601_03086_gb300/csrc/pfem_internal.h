@@ -216,6 +216,7 @@ struct PcgArgs {
   unsigned int* ticket;   // zero-initialised; reset by the last tile
   double beta;            // OP_PERSIST: beta of this iteration
   int odd;                // OP_PERSIST: parity of the completed iteration count
+  int alpha_by_update;    // 1: tiles only store their sums; the update kernel forms alpha
 };
 
 // Grid barrier of the persistent PCG kernel (zeroed before every launch).

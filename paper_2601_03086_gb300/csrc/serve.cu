@@ -479,6 +479,7 @@ pfem_status rebuild_tables(pfem_server_s* S) {
     d.pcg.st = R->st;
     d.pcg.tile_part = R->tile_part;
     d.pcg.ticket = R->ticket_dev;
+    d.pcg.alpha_by_update = 0;  // alpha by each solve's last tile
     d.q = R->q;
     d.x = R->x;
     d.u = R->solve_kind == PFEM_SOLVE_NEWTON ? R->u : nullptr;

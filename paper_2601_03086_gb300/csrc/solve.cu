@@ -124,10 +124,11 @@ static pfem_status pcg_body(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_
   a.pcg.st = w->st;
   a.pcg.tile_part = w->tile_part;
   a.pcg.ticket = w->ticket;
+  a.pcg.alpha_by_update = 1;  // the update kernel forms alpha from the tile sums
   pfem_status st = launch_element_op(m->plan, OP_TANGENT | OP_PCG, PFEM_F64, ct, a, s);
   if (st) return st;
-  return vk_update(w->n, w->x, w->r, w->p, w->p2, w->q, w->dinv, w->st, m->red_partials, m->red_counter, h, set_cond,
-                   s);
+  return vk_update(w->n, w->x, w->r, w->p, w->p2, w->q, w->dinv, w->st, w->tile_part, (int)m->plan.n_tiles,
+                   m->red_partials, m->red_counter, h, set_cond, s);
 }
 
 // PCG iterations per replay of the graph's while-loop body (fewer conditional-node

@@ -451,10 +451,13 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
       odd = A.pcg.odd != 0;
     } else {
       // the state is written only by earlier kernels, so every CTA takes the same branch
+      // (all four fields loaded before the branch: one round trip)
       const PcgState* st = A.pcg.st;
-      if (st->done != 0 || st->repl != 0) return;
-      beta = st->beta;
-      odd = (st->iter & 1) != 0;
+      const int done = st->done, repl = st->repl, it = st->iter;
+      const double b = st->beta;
+      if (done != 0 || repl != 0) return;
+      beta = b;
+      odd = (it & 1) != 0;
     }
     // select, not index: keeps the arguments out of local memory
     p_old = odd ? A.pcg.p[1] : A.pcg.p[0];
@@ -617,6 +620,8 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
   }
   if constexpr (PCG) {
     // the last tile to finish sums the tile partials in tile order: alpha = rho / (p . A p)
+    // (unless the update kernel forms alpha itself from the same partials)
+    if (A.pcg.alpha_by_update) return;
     __shared__ bool s_last;
     if (threadIdx.x == 0) {
       __threadfence();
@@ -625,28 +630,21 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
     __syncthreads();
     if (s_last) {
       __threadfence();
-      double s = 0.0;
-      for (int i = threadIdx.x; i < P.n_tiles; i += blockDim.x) s += __ldcg(A.pcg.tile_part + i);
-      double* red = reinterpret_cast<double*>(smem + L.red);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      __syncthreads();
-      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-      __syncthreads();
+      // thread 0's state reads go out with the tile partials' loads
+      PcgState* st = A.pcg.st;
+      double rho = 0.0;
+      int trunc = 0, it = 0;
       if (threadIdx.x == 0) {
-        double pap = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pap += red[w];
-        PcgState* st = A.pcg.st;
-        // negative curvature does not stop plain CG; p.Ap = 0 or non-finite does
-        if (pap == 0.0 || !isfinite(pap)) {
-          st->alpha = 0.0;
-          st->done = isfinite(pap) ? PCG_BREAKDOWN : PCG_NONFINITE;
-        } else if (pap < 0.0 && __ldcg(&st->truncate) != 0 && __ldcg(&st->iter) > 0) {
-          st->alpha = 0.0;  // truncated CG: keep the iterate reached with positive curvature
-          st->done = PCG_NEGCURV;
-        } else {
-          st->alpha = __ldcg(&st->rho) / pap;
-        }
+        rho = __ldcg(&st->rho);
+        trunc = __ldcg(&st->truncate);
+        it = __ldcg(&st->iter);
+      }
+      const double pap = pcg_tile_total(A.pcg.tile_part, P.n_tiles, reinterpret_cast<double*>(smem + L.red));
+      if (threadIdx.x == 0) {
+        double alpha = 0.0;
+        const int stop = pcg_alpha(pap, rho, trunc, it, &alpha);
+        st->alpha = alpha;
+        if (stop) st->done = stop;
         *A.pcg.ticket = 0u;
       }
     }
