@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda/atomic>
 
 #include "pfem_internal.h"
 
@@ -44,13 +45,13 @@ __device__ __forceinline__ bool grid_sum_v(double (&v)[N], double* partials, uns
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < N; ++k) partials[vb * N + k] = v[k];
-    __threadfence();
-    const unsigned t = atomicAdd(counter, 1u);
+    // release: the partials before the count; acquire: the last block sees every partial
+    const unsigned t =
+        cuda::atomic_ref<unsigned int, cuda::thread_scope_device>(*counter).fetch_add(1u, cuda::memory_order_acq_rel);
     s_last = (t == (unsigned)nvb - 1u);
   }
   __syncthreads();
-  if (!s_last) return false;
-  __threadfence();
+  if (!s_last) return false;  // (thread 0's acquire + the barrier order the loads below)
   double acc[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) acc[k] = 0.0;
