@@ -109,6 +109,10 @@ typedef struct {
   int64_t kernel_launches;         /* kernels this solve ran (graph replays included) */
   double queue_s;                  /* serving: submit -> admission (s) */
   double total_s;                  /* serving: submit -> result ready (s) */
+  double apply_ms;                 /* kernel timing on, plain loop: summed PCG-fused apply time */
+  double update_ms;                /* kernel timing on, plain loop: summed update-kernel time */
+  int32_t timed_iterations;        /* iterations those sums cover (0 = not timed) */
+  int32_t reserved;
 } pfem_solve_info;
 
 /* ---- mesh ------------------------------------------------------------------------ */
@@ -202,6 +206,13 @@ pfem_status pfem_solve_newton(pfem_mesh_t mesh, pfem_dtype dtype, const double* 
  * baseline). 2 (default): the iteration captured as a CUDA graph with a device-side while
  * loop. Other values: PFEM_ERR_INVALID_ARG. */
 pfem_status pfem_set_solver_mode(int32_t mode);
+
+/* Per-kernel timing of later solves (process-wide; 1 = on, 0 = off, the default; other
+ * values PFEM_ERR_INVALID_ARG). While on, the plain loop (solver mode 1) brackets the two
+ * kernels of every PCG iteration with CUDA events on the mesh's stream and reports their
+ * summed durations in pfem_solve_info (apply_ms, update_ms, timed_iterations); the graph
+ * and persistent loops are not timed. */
+pfem_status pfem_set_kernel_timing(int32_t on);
 
 /* ---- ragged batch: energy loss, gradient and Hessian-vector product in one launch --- */
 

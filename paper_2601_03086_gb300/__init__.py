@@ -27,6 +27,7 @@ from .api import (  # noqa: F401
     pfem_mesh_set_load_scale,
     pfem_plan_check,
     pfem_residual,
+    pfem_set_kernel_timing,
     pfem_set_solver_mode,
     pfem_solve_linear,
     pfem_solve_newton,

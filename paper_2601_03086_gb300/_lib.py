@@ -77,6 +77,10 @@ class SolveInfo(C.Structure):
         ("kernel_launches", C.c_int64),
         ("queue_s", C.c_double),
         ("total_s", C.c_double),
+        ("apply_ms", C.c_double),
+        ("update_ms", C.c_double),
+        ("timed_iterations", C.c_int32),
+        ("reserved", C.c_int32),
     ]
 
 
@@ -97,6 +101,7 @@ SIGNATURES = {
     "pfem_solve_newton": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_int32,
                                       C.c_double, C.c_void_p, C.POINTER(SolveInfo)]),
     "pfem_set_solver_mode": (C.c_int32, [C.c_int32]),
+    "pfem_set_kernel_timing": (C.c_int32, [C.c_int32]),
     "pfem_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "pfem_batch_destroy": (None, [C.c_void_p]),
     "pfem_batch_offsets": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64)]),

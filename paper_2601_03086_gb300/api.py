@@ -194,6 +194,10 @@ def pfem_set_solver_mode(mode):
     check(lib().pfem_set_solver_mode(int(mode)))
 
 
+def pfem_set_kernel_timing(on):
+    check(lib().pfem_set_kernel_timing(int(on)))
+
+
 def pfem_version():
     return lib().pfem_version().decode()
 

@@ -47,7 +47,14 @@ struct SolverWS {
   int64_t body_kernels[2][2] = {{0, 0}, {0, 0}};  // kernels per captured iteration
   bool graph_failed = false;
   bool persist_failed[2] = {false, false};  // [use_u]
+  // kernel timing (plain loop): events around the apply and the update of an iteration
+  cudaEvent_t tev[3] = {nullptr, nullptr, nullptr};
+  bool t_pending = false;
+  double t_apply_ms = 0.0, t_update_ms = 0.0;
+  int t_n = 0;
 };
+
+static int g_kernel_timing = 0;
 
 __global__ void set_cond_kernel(cudaGraphConditionalHandle h, const PcgState* st) {
   cudaGraphSetConditional(h, (st->done == 0 && st->repl == 0) ? 1u : 0u);
@@ -69,6 +76,8 @@ void solver_release(pfem_mesh_t m) {
     for (auto& e : row)
       if (e) cudaGraphExecDestroy(e);
   if (w->cap) cudaStreamDestroy(w->cap);
+  for (cudaEvent_t e : w->tev)
+    if (e) cudaEventDestroy(e);
   if (w->block) cudaFree(w->block);
   if (w->hst) cudaFreeHost(w->hst);
   delete w;
@@ -114,8 +123,9 @@ static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
 
 // One PCG iteration in two kernels: the fused apply (p = dinv r + beta p_old, q = A p,
 // alpha = rho / p.Ap) and the update (x += alpha p, r -= alpha q, rho, beta, flags).
+// ev (plain loop, kernel timing): three events recorded before, between and after the kernels.
 static pfem_status pcg_body(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u, cudaStream_t s,
-                            cudaGraphConditionalHandle h, int set_cond) {
+                            cudaGraphConditionalHandle h, int set_cond, cudaEvent_t* ev = nullptr) {
   OpArgs a{use_u ? w->u : nullptr, nullptr, w->q, nullptr, nullptr, 1.0};
   a.pcg.r = w->r;
   a.pcg.dinv = w->dinv;
@@ -125,10 +135,15 @@ static pfem_status pcg_body(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_
   a.pcg.tile_part = w->tile_part;
   a.pcg.ticket = w->ticket;
   a.pcg.alpha_by_update = 1;  // the update kernel forms alpha from the tile sums
+  if (ev) PFEM_CUDA(cudaEventRecord(ev[0], s));
   pfem_status st = launch_element_op(m->plan, OP_TANGENT | OP_PCG, PFEM_F64, ct, a, s);
   if (st) return st;
-  return vk_update(w->n, w->x, w->r, w->p, w->p2, w->q, w->dinv, w->st, w->tile_part, (int)m->plan.n_tiles,
-                   m->red_partials, m->red_counter, h, set_cond, s);
+  if (ev) PFEM_CUDA(cudaEventRecord(ev[1], s));
+  st = vk_update(w->n, w->x, w->r, w->p, w->p2, w->q, w->dinv, w->st, w->tile_part, (int)m->plan.n_tiles,
+                 m->red_partials, m->red_counter, h, set_cond, s);
+  if (st) return st;
+  if (ev) PFEM_CUDA(cudaEventRecord(ev[2], s));
+  return PFEM_OK;
 }
 
 // PCG iterations per replay of the graph's while-loop body (fewer conditional-node
@@ -231,6 +246,15 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
   int64_t pending_body = 0;
   for (;;) {
     if ((st = read_state(m, w))) return st;
+    if (w->t_pending) {  // the timed iteration has completed (read_state synchronised)
+      float a = 0.f, b = 0.f;
+      PFEM_CUDA(cudaEventElapsedTime(&a, w->tev[0], w->tev[1]));
+      PFEM_CUDA(cudaEventElapsedTime(&b, w->tev[1], w->tev[2]));
+      w->t_apply_ms += a;
+      w->t_update_ms += b;
+      ++w->t_n;
+      w->t_pending = false;
+    }
     if (pending_bodies0 >= 0) {  // a graph launch ran (body replays x body) + the pre-node
       g_kernel_launches += (int64_t)(w->hst->bodies - pending_bodies0) * pending_body + 1;
       pending_bodies0 = -1;
@@ -278,10 +302,26 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
       pending_body = w->body_kernels[ct == PFEM_F64][ui];
       PFEM_CUDA(cudaGraphLaunch(*ex, s));
     } else {
-      if ((st = pcg_body(m, w, ct, use_u, s, cudaGraphConditionalHandle(), 0))) return st;
+      const bool timed = g_kernel_timing != 0;
+      if (timed && !w->tev[0])
+        for (cudaEvent_t& e : w->tev) PFEM_CUDA(cudaEventCreate(&e));
+      if ((st = pcg_body(m, w, ct, use_u, s, cudaGraphConditionalHandle(), 0, timed ? w->tev : nullptr))) return st;
+      w->t_pending = timed;
     }
   }
   return PFEM_OK;
+}
+
+static void timing_reset(SolverWS* w) {
+  w->t_pending = false;
+  w->t_apply_ms = w->t_update_ms = 0.0;
+  w->t_n = 0;
+}
+
+static void timing_report(const SolverWS* w, pfem_solve_info* info) {
+  info->apply_ms = w->t_apply_ms;
+  info->update_ms = w->t_update_ms;
+  info->timed_iterations = w->t_n;
 }
 
 static pfem_status set_state(pfem_mesh_t m, SolverWS* w, double tol, int max_iter, int truncate = 0) {
@@ -346,6 +386,15 @@ pfem_status pfem_set_solver_mode(int32_t mode) {
   return PFEM_OK;
 }
 
+pfem_status pfem_set_kernel_timing(int32_t on) {
+  if (on != 0 && on != 1) {
+    set_error("kernel timing must be 0 (off) or 1 (on)");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  g_kernel_timing = on;
+  return PFEM_OK;
+}
+
 pfem_status pfem_solve_linear(pfem_mesh_t m, pfem_dtype dt, const double* u0, double tol, int32_t max_iter,
                               double* u_out, pfem_solve_info* info) {
   pfem_status st = check_mesh(m);
@@ -361,6 +410,7 @@ pfem_status pfem_solve_linear(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
   SolverWS* w;
   const int64_t launches0 = g_kernel_launches;
   if ((st = ws_get(m, &w))) return st;
+  timing_reset(w);
   cudaStream_t s = m->stream;
   if ((st = set_state(m, w, tol, max_iter))) return st;
   if ((st = reference_norm(m, w, m->load_scale))) return st;
@@ -382,6 +432,7 @@ pfem_status pfem_solve_linear(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
   if (info) {
     info->status = st;
     info->kernel_launches = g_kernel_launches - launches0;
+    timing_report(w, info);
   }
   if (st) set_error("PCG stopped with state %d after %d iterations (rel %g)", h.done, h.iter, h.rel_true);
   return st;
@@ -399,6 +450,7 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
   SolverWS* w;
   const int64_t launches0 = g_kernel_launches;
   if ((st = ws_get(m, &w))) return st;
+  timing_reset(w);
   cudaStream_t s = m->stream;
   const double saved_scale = m->load_scale;
   const int64_t n = w->n;
@@ -495,6 +547,7 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
     info->reference_norm = ref;
     info->status = result;
     info->kernel_launches = g_kernel_launches - launches0;
+    timing_report(w, info);
   }
   return result;
 }

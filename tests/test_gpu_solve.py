@@ -96,6 +96,31 @@ def test_solver_modes_bitwise_equal_newton_and_2d():
             assert outs[0][1] == o[1], kind
 
 
+def test_kernel_timing_plain_loop():
+    """Kernel timing times every plain-loop iteration's two kernels, changes no bit of the
+    solve, and leaves graph solves untimed."""
+    P = pfem()
+    p = pi.cube_problem(8, seed=3)
+    mesh = P.Mesh(p)
+    try:
+        P.pfem_set_solver_mode(1)
+        u0, i0 = P.pfem_solve_linear(mesh, tol=1e-8)
+        assert i0["timed_iterations"] == 0 and i0["apply_ms"] == 0.0
+        P.pfem_set_kernel_timing(1)
+        u1, i1 = P.pfem_solve_linear(mesh, tol=1e-8)
+        assert np.array_equal(host(u0), host(u1)) and i1["iterations"] == i0["iterations"]
+        assert i1["timed_iterations"] == i1["iterations"]
+        assert i1["apply_ms"] > 0.0 and i1["update_ms"] > 0.0
+        P.pfem_set_solver_mode(2)
+        _, i2 = P.pfem_solve_linear(mesh, tol=1e-8)
+        assert i2["timed_iterations"] == 0
+    finally:
+        P.pfem_set_kernel_timing(0)
+        P.pfem_set_solver_mode(2)
+    with pytest.raises(RuntimeError):
+        P.pfem_set_kernel_timing(2)
+
+
 def test_solver_mode_rejects_unknown():
     P = pfem()
     with pytest.raises(RuntimeError):
