@@ -354,6 +354,15 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
   const PcgState& ps = sl.st;
   pfem_status st = PFEM_OK;
   auto fail = [&](pfem_status e) {
+    if (e != PFEM_OK && R->solve_kind != PFEM_SOLVE_LINEAR) {  // the work done before the failure
+      R->info.iterations = R->inner_iters;
+      R->info.newton_iterations = R->newton;
+      R->info.replacements = R->repl;
+      R->info.inverted_backtracks = R->backtracks;
+      R->info.rel_residual_recursive = R->last_rel;
+      R->info.initial_rel_residual = R->init_rel;
+      R->info.reference_norm = R->ref;
+    }
     finish(S, R, e);
     return false;
   };
