@@ -112,7 +112,7 @@ typedef struct {
   double apply_ms;                 /* kernel timing on, plain loop: summed PCG-fused apply time */
   double update_ms;                /* kernel timing on, plain loop: summed update-kernel time */
   int32_t timed_iterations;        /* iterations those sums cover (0 = not timed) */
-  int32_t reserved;
+  int32_t load_step_cuts;          /* Newton: load increments halved after a failed level */
 } pfem_solve_info;
 
 /* ---- mesh ------------------------------------------------------------------------ */
@@ -192,7 +192,11 @@ pfem_status pfem_solve_linear(pfem_mesh_t mesh, pfem_dtype dtype, const double* 
  * (App. B); a warm start passes u0 = U^NO and n_load_steps = 1, bypassing the earlier
  * steps. Residuals and updates in FP64; tangent applies in dtype; inner Jacobi-PCG to
  * inner_tol relative to the current residual. Step halving (<= 10) when a trial makes
- * J <= 0, else INVERTED. u0/u_out: FP64 device vectors (may alias, u0 NULL = zero). */
+ * J <= 0. A load level that still fails (every halving inverts an element, max_newton
+ * iterations without convergence, or a non-finite residual) is retried from the last
+ * converged state with half the load increment (at most 8 times per solve, reported in
+ * info->load_step_cuts); then INVERTED / NOT_CONVERGED / NONFINITE. u0/u_out: FP64 device
+ * vectors (may alias, u0 NULL = zero). */
 pfem_status pfem_solve_newton(pfem_mesh_t mesh, pfem_dtype dtype, const double* u0, double tol,
                               int32_t n_load_steps, int32_t max_newton, double inner_tol,
                               double* u_out, pfem_solve_info* info);

@@ -80,7 +80,7 @@ class SolveInfo(C.Structure):
         ("apply_ms", C.c_double),
         ("update_ms", C.c_double),
         ("timed_iterations", C.c_int32),
-        ("reserved", C.c_int32),
+        ("load_step_cuts", C.c_int32),
     ]
 
 

@@ -38,6 +38,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include <string>
@@ -306,6 +307,40 @@ pfem_status launch_element_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dty
 
 // Launches the persistent PCG kernel (FP32 element arithmetic only); PFEM_ERR_UNSUPPORTED
 // when it cannot run here (other arithmetic, no co-resident grid), without side effects.
+// Load levels of Newton's load stepping (App. B: equal steps of 1/n). A level whose Newton
+// iteration fails (every step halving inverts an element, no convergence, or a non-finite
+// residual) is retried from the last converged state with half the load increment, at most
+// kMaxLoadCuts times per solve; each converged level doubles the increment back (up to 1/n).
+// Levels are integers over n * 2^kCutBits, so without cuts the load fractions are exactly
+// step / n.
+constexpr int kMaxLoadCuts = 8;
+struct LoadSchedule {
+  static constexpr int kCutBits = 6;
+  int64_t den = 1, prev = 0, inc = 1, cur = 1;
+  int cuts = 0;
+  void start(int n_steps) {
+    den = (int64_t)n_steps << kCutBits;
+    inc = int64_t(1) << kCutBits;
+    prev = 0;
+    cur = inc;
+    cuts = 0;
+  }
+  double fraction() const { return (double)cur / (double)den; }
+  bool last() const { return cur == den; }
+  void converged() {  // the current level converged and is not the last
+    prev = cur;
+    inc = std::min<int64_t>(inc * 2, int64_t(1) << kCutBits);
+    cur = std::min(den, prev + inc);
+  }
+  bool cut() {  // retry the current level with half the increment; false when out of cuts
+    if (inc <= 1 || cuts >= kMaxLoadCuts) return false;
+    ++cuts;
+    inc /= 2;
+    cur = prev + inc;
+    return true;
+  }
+};
+
 pfem_status launch_pcg_persistent(const DevPlan& P, pfem_dtype ct, const PersistArgs& a, cudaStream_t s);
 
 // Halo partials from which launch_element_op completes halo nodes in a separate pass instead

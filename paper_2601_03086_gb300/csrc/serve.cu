@@ -105,6 +105,7 @@ struct Request {
   void* block = nullptr;
   double *x = nullptr, *r = nullptr, *p0 = nullptr, *p1 = nullptr, *q = nullptr, *dinv = nullptr;
   double *res = nullptr, *u = nullptr, *rn = nullptr, *tmp = nullptr, *tile_part = nullptr, *upart = nullptr;
+  double* uc = nullptr;  // Newton: state at the last converged load level
   double* aux = nullptr;
   unsigned *ticket_dev = nullptr, *ucount = nullptr;
   PcgState* st = nullptr;
@@ -112,7 +113,8 @@ struct Request {
   int64_t n = 0;
   // state machine
   Phase phase = PH_LIN_RUN;
-  int step = 1;
+  LoadSchedule load;
+  int level_newton = 0;  // Newton steps at the current load level
   double ref = 1.0, t_ls = 1.0;
   int newton = 0, inner_iters = 0, repl = 0, backtracks = 0, ls_tries = 0;
   double init_rel = -1.0, last_rel = 0.0;
@@ -184,7 +186,7 @@ pfem_status grow(void** p, size_t* cap, size_t need, size_t elem) {
 size_t request_bytes(const HostPlan& hp) {
   const int64_t n = hp.n_nodes * hp.dim;
   const size_t vb = ((size_t)n * 8 + 255) & ~size_t(255);
-  return mesh_arena_bytes(hp) + 10 * vb + (size_t)hp.n_tiles() * 8 + 296 * 16 + 4096;
+  return mesh_arena_bytes(hp) + 11 * vb + (size_t)hp.n_tiles() * 8 + 296 * 16 + 4096;
 }
 
 pfem_status admit(pfem_server_s* S, Request* R) {
@@ -195,15 +197,15 @@ pfem_status admit(pfem_server_s* S, Request* R) {
   const size_t vb = ((size_t)R->n * 8 + 255) & ~size_t(255);
   const size_t tb = ((size_t)std::max(R->mesh->plan.n_tiles, 1) * 8 + 255) & ~size_t(255);
   const size_t ub = ((size_t)R->nublk * 16 + 255) & ~size_t(255);
-  const size_t bytes = 10 * vb + tb + ub + 1024;
+  const size_t bytes = 11 * vb + tb + ub + 1024;
   cudaError_t e = cudaMallocFromPoolAsync(&R->block, bytes, S->pool, S->stream);
   if (e != cudaSuccess) return cuda_fail(e, "device allocation (serving workspace)");
   char* b = static_cast<char*>(R->block);
-  double** v[10] = {&R->x, &R->r, &R->p0, &R->p1, &R->q, &R->dinv, &R->res, &R->u, &R->rn, &R->tmp};
-  for (int i = 0; i < 10; ++i) *v[i] = reinterpret_cast<double*>(b + i * vb);
-  R->tile_part = reinterpret_cast<double*>(b + 10 * vb);
-  R->upart = reinterpret_cast<double*>(b + 10 * vb + tb);
-  char* tail = b + 10 * vb + tb + ub;
+  double** v[11] = {&R->x, &R->r, &R->p0, &R->p1, &R->q, &R->dinv, &R->res, &R->u, &R->rn, &R->tmp, &R->uc};
+  for (int i = 0; i < 11; ++i) *v[i] = reinterpret_cast<double*>(b + i * vb);
+  R->tile_part = reinterpret_cast<double*>(b + 11 * vb);
+  R->upart = reinterpret_cast<double*>(b + 11 * vb + tb);
+  char* tail = b + 11 * vb + tb + ub;
   R->st = reinterpret_cast<PcgState*>(tail);
   R->aux = reinterpret_cast<double*>(tail + 256);
   R->ticket_dev = reinterpret_cast<unsigned*>(tail + 512);
@@ -272,7 +274,7 @@ pfem_status enq_jacobi(Request* R, const double* u, cudaStream_t s) {
   return vk_invert_diag(R->n, R->q, PFEM_F64, R->dinv, s);
 }
 
-double load_scale_of(const Request* R) { return (double)R->step / (double)R->n_load_steps; }
+double load_scale_of(const Request* R) { return R->load.fraction(); }
 
 // Newton: reference norm of this load step (lift the prescribed values first)
 pfem_status enq_newton_step(Request* R, cudaStream_t s) {
@@ -322,7 +324,9 @@ pfem_status start_solve(Request* R, cudaStream_t s) {
     R->phase = PH_LIN_RUN;
     return PFEM_OK;
   }
-  R->step = 1;
+  R->load.start(R->n_load_steps);
+  R->level_newton = 0;
+  PFEM_CUDA(cudaMemcpyAsync(R->uc, R->u, (size_t)R->n * 8, cudaMemcpyDeviceToDevice, s));
   return enq_newton_step(R, s);
 }
 
@@ -363,8 +367,20 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
       R->info.initial_rel_residual = R->init_rel;
       R->info.reference_norm = R->ref;
     }
+    R->info.load_step_cuts = R->load.cuts;
     finish(S, R, e);
     return false;
+  };
+  // a failed Newton load level: again from the last converged state with half the
+  // increment, or the failure when the cuts are used up
+  auto retry_level = [&](pfem_status e) {
+    if (!R->load.cut()) return fail(e);
+    if (cudaMemcpyAsync(R->u, R->uc, (size_t)R->n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return fail(PFEM_ERR_CUDA);
+    R->level_newton = 0;
+    const pfem_status st2 = enq_newton_step(R, s);
+    if (st2) return fail(st2);
+    return true;
   };
   switch (R->phase) {
     case PH_LIN_RUN:
@@ -392,10 +408,15 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
       const double rel = sl.aux[1] / R->ref;
       if (R->init_rel < 0) R->init_rel = rel;
       R->last_rel = rel;
-      if (!std::isfinite(rel)) return fail(PFEM_ERR_NONFINITE);
+      if (!std::isfinite(rel)) return retry_level(PFEM_ERR_NONFINITE);
       if (rel <= R->tol) {
-        if (R->step < R->n_load_steps) {
-          R->step++;
+        if (!R->load.last()) {  // next load level from this converged state
+          R->load.converged();
+          R->level_newton = 0;
+          if (cudaMemcpyAsync(R->uc, R->u, (size_t)R->n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+            st = PFEM_ERR_CUDA;
+            break;
+          }
           st = enq_newton_step(R, s);
           break;
         }
@@ -409,7 +430,7 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
         R->info.reference_norm = R->ref;
         return fail(PFEM_OK);
       }
-      if (R->newton >= 50 * R->n_load_steps) return fail(PFEM_ERR_NOT_CONVERGED);
+      if (R->level_newton >= 50) return retry_level(PFEM_ERR_NOT_CONVERGED);
       // inner solve A(u) d = -rn from d = 0 to 1e-8 relative to ||rn||
       if ((st = enq_jacobi(R, R->u, s))) break;
       if (cudaMemsetAsync(R->x, 0, (size_t)R->n * 8, s) != cudaSuccess) {
@@ -442,7 +463,7 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
         R->ls_tries = 0;
         st = enq_line_search(R, s);
       } else if (ps.done != 0) {
-        return fail(ps.done == PCG_NONFINITE ? PFEM_ERR_NONFINITE : PFEM_ERR_NOT_CONVERGED);
+        return retry_level(ps.done == PCG_NONFINITE ? PFEM_ERR_NONFINITE : PFEM_ERR_NOT_CONVERGED);
       } else if (ps.repl) {
         st = enq_replacement(R, true, s);
       }
@@ -452,13 +473,14 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
       if (sl.inverted == 0) {
         cudaMemcpyAsync(R->u, R->tmp, (size_t)R->n * 8, cudaMemcpyDeviceToDevice, s);
         R->newton++;
+        R->level_newton++;
         st = enq_newton_check(R, s);
       } else if (++R->ls_tries <= 10) {
         R->backtracks++;
         R->t_ls *= 0.5;
         st = enq_line_search(R, s);
       } else {
-        return fail(PFEM_ERR_INVERTED);
+        return retry_level(PFEM_ERR_INVERTED);
       }
       break;
     default:

@@ -34,6 +34,7 @@ struct SolverWS {
   int64_t n = 0;
   double *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *dinv = nullptr, *res = nullptr;
   double *u = nullptr, *rn = nullptr, *tmp = nullptr, *p2 = nullptr;
+  double* uc = nullptr;              // Newton: state at the last converged load level
   double* tile_part = nullptr;       // per-tile p . A p partials of the fused apply
   unsigned int* ticket = nullptr;    // last-tile ticket of the fused apply
   GridBar* bar = nullptr;            // grid barrier of the persistent kernel
@@ -93,20 +94,20 @@ static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
   w->n = m->n_dofs;
   const size_t vb = ((size_t)w->n * sizeof(double) + 255) & ~size_t(255);
   const size_t tb = ((size_t)std::max(m->plan.n_tiles, 1) * sizeof(double) + 255) & ~size_t(255);
-  w->bytes = 10 * vb + tb + 768;
+  w->bytes = 11 * vb + tb + 768;
   cudaError_t e = cudaMalloc(&w->block, w->bytes);
   if (e != cudaSuccess) {
     delete w;
     return cuda_fail(e, "cudaMalloc(solver workspace)");
   }
   char* b = static_cast<char*>(w->block);
-  double** vecs[10] = {&w->x, &w->r, &w->p, &w->q, &w->dinv, &w->res, &w->u, &w->rn, &w->tmp, &w->p2};
-  for (int i = 0; i < 10; ++i) *vecs[i] = reinterpret_cast<double*>(b + i * vb);
-  w->tile_part = reinterpret_cast<double*>(b + 10 * vb);
-  w->st = reinterpret_cast<PcgState*>(b + 10 * vb + tb);
-  w->dnorm = reinterpret_cast<double*>(b + 10 * vb + tb + 256);
-  w->ticket = reinterpret_cast<unsigned int*>(b + 10 * vb + tb + 512);
-  w->bar = reinterpret_cast<GridBar*>(b + 10 * vb + tb + 640);
+  double** vecs[11] = {&w->x, &w->r, &w->p, &w->q, &w->dinv, &w->res, &w->u, &w->rn, &w->tmp, &w->p2, &w->uc};
+  for (int i = 0; i < 11; ++i) *vecs[i] = reinterpret_cast<double*>(b + i * vb);
+  w->tile_part = reinterpret_cast<double*>(b + 11 * vb);
+  w->st = reinterpret_cast<PcgState*>(b + 11 * vb + tb);
+  w->dnorm = reinterpret_cast<double*>(b + 11 * vb + tb + 256);
+  w->ticket = reinterpret_cast<unsigned int*>(b + 11 * vb + tb + 512);
+  w->bar = reinterpret_cast<GridBar*>(b + 11 * vb + tb + 640);
   e = cudaMemset(w->ticket, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMallocHost(&w->hst, sizeof(PcgState));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&w->cap, cudaStreamNonBlocking);
@@ -460,8 +461,11 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
   if (u0) PFEM_CUDA(cudaMemcpyAsync(w->u, u0, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   else PFEM_CUDA(cudaMemsetAsync(w->u, 0, (size_t)n * sizeof(double), s));
   const int inner_max = (int)std::min<int64_t>(10 * n + 100, kInnerMaxIter);
-  for (int step = 1; step <= n_load_steps && result == PFEM_OK; ++step) {
-    const double scale = saved_scale * (double)step / (double)n_load_steps;
+  LoadSchedule ls;
+  ls.start(n_load_steps);
+  PFEM_CUDA(cudaMemcpyAsync(w->uc, w->u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  for (;;) {
+    const double scale = saved_scale * ls.fraction();
     m->load_scale = scale;
     if ((st = vk_lift(n, w->u, m->plan.dvalues, m->plan.dmask, scale, w->u, s))) break;
     if ((st = set_state(m, w, inner_tol, inner_max))) break;
@@ -484,7 +488,7 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
       if (rel <= tol) break;
       if (it >= max_newton) {
         result = PFEM_ERR_NOT_CONVERGED;
-        set_error("Newton: %d iterations in load step %d, rel residual %g", it, step, rel);
+        set_error("Newton: %d iterations at load fraction %g, rel residual %g", it, ls.fraction(), rel);
         break;
       }
       // inner solve A(u) d = -rn from d = 0 to inner_tol relative to ||rn||
@@ -530,6 +534,16 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
       ++n_newton;
     }
     if (st) break;
+    if (result == PFEM_OK) {  // this level converged
+      if (ls.last()) break;
+      ls.converged();
+      PFEM_CUDA(cudaMemcpyAsync(w->uc, w->u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      continue;
+    }
+    const bool retry = result == PFEM_ERR_INVERTED || result == PFEM_ERR_NOT_CONVERGED || result == PFEM_ERR_NONFINITE;
+    if (!retry || !ls.cut()) break;
+    result = PFEM_OK;  // again from the last converged state with half the increment
+    PFEM_CUDA(cudaMemcpyAsync(w->u, w->uc, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   m->load_scale = saved_scale;
   if (st) return st;
@@ -547,6 +561,7 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
     info->reference_norm = ref;
     info->status = result;
     info->kernel_launches = g_kernel_launches - launches0;
+    info->load_step_cuts = ls.cuts;
     timing_report(w, info);
   }
   return result;

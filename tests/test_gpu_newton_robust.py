@@ -43,3 +43,26 @@ def test_two_load_steps_bounded_work(bar):
         m = fem.Mesh(bar)
         r = fem.residual(m, u.cpu().numpy(), 1.0)
         assert np.isfinite(r).all()
+
+
+def test_load_cuts_with_one_newton_step_per_level(bar):
+    """max_newton = 1 gives every load level a single Newton step: failed levels are retried
+    from the last converged state with half the increment until the cuts run out (then
+    NOT_CONVERGED), or the halved levels converge and the solution is the oracle's."""
+    P = pfem()
+    mesh = P.Mesh(bar)
+    u, info = P.pfem_solve_newton(mesh, tol=1e-8, n_load_steps=1, max_newton=1, raise_on_error=False)
+    assert 1 <= info["load_step_cuts"] <= 8, info
+    if info["status"] == 0:
+        m = fem.Mesh(bar)
+        u_ref, _, _ = solve.solve_newton(m, tol=1e-8, n_load_steps=5, direct=True)
+        assert rel_l2(u.cpu().numpy(), u_ref) <= 1e-6
+    else:
+        assert info["status"] == 5, info  # PFEM_ERR_NOT_CONVERGED
+
+
+def test_no_cuts_when_levels_converge(bar):
+    P = pfem()
+    mesh = P.Mesh(bar)
+    _, info = P.pfem_solve_newton(mesh, tol=1e-8, n_load_steps=5)
+    assert info["status"] == 0 and info["load_step_cuts"] == 0
