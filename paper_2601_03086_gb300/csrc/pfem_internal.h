@@ -206,15 +206,15 @@ struct PcgState {
 
 // Extra inputs of the PCG-fused tangent apply (OP_PCG): the search direction is formed on
 // the fly, p = dinv r + beta p_old, written to p[(iter + 1) & 1], and A p goes to y; each tile
-// also sums p_e . (A_e p_e) over its elements, and the last tile turns the tile sums into
-// alpha = rho / (p . A p).
+// also sums p_e . (A_e p_e) over its elements; alpha = rho / (p . A p) is formed from the
+// tile sums either by the last tile (ticket) or, with alpha_by_update, by the update kernel.
 struct PcgArgs {
   const double* r;
   const double* dinv;
   double* p[2];           // direction buffers (p_old = p[iter & 1])
   PcgState* st;
   double* tile_part;      // n_tiles doubles
-  unsigned int* ticket;   // zero-initialised; reset by the last tile
+  unsigned int* ticket;   // zero-initialised; reset by the last tile (unused with alpha_by_update)
   double beta;            // OP_PERSIST: beta of this iteration
   int odd;                // OP_PERSIST: parity of the completed iteration count
   int alpha_by_update;    // 1: tiles only store their sums; the update kernel forms alpha
