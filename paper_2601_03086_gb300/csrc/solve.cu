@@ -454,6 +454,11 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
   timing_reset(w);
   cudaStream_t s = m->stream;
   const double saved_scale = m->load_scale;
+  struct ScaleRestore {  // the caller's load scale comes back on every return path
+    pfem_mesh_t m;
+    double v;
+    ~ScaleRestore() { m->load_scale = v; }
+  } restore{m, saved_scale};
   const int64_t n = w->n;
   int total_inner = 0, n_newton = 0, n_repl = 0, n_back = 0;
   double init_rel = -1.0, final_rel = 0.0, ref = 1.0;
