@@ -18,6 +18,15 @@ dominant kernel (element tangent apply), the same kernel on the 160^3 cube (24.6
 beyond L2), the Neo-Hookean Newton solves of the 64x16x16 bar, and the FP64 CPU oracle
 timed on this host.
 
+--probe apply|solve runs one kernel-level driver instead (for ncu captures and quick timing):
+    --probe apply --n 160 --reps 3 [--vec f64] [--kind nh] [--op residual]
+        tangent apply (or residual) on the n^3 x 6 Kuhn cube (FP32 element arithmetic;
+        f64 = FP64 vectors with FP32 arithmetic, the PCG configuration)
+    --probe solve --n 40 --max-iter 40 [--solver-mode plain]
+        Jacobi-PCG solves of the n^3 cube (the benchmark workload at n = 40); plain runs one
+        kernel at a time, so that a profiler attributes time per kernel
+  and prints one JSON line with CUDA-event timings after warm-up.
+
 --impl reference times the FP64 CPU oracle (global sparse assembly + Jacobi-PCG) on the
 same workload: each step is a bounded sample of 100 PCG iterations of a warm solve,
 projected to the oracle's full iteration count (measured once in the warm-up).
@@ -217,10 +226,20 @@ def main():
                     help="graph (device while loop, default), persistent (one cooperative launch per "
                          "replacement interval) or plain (one launch per kernel, for profiler launch lists)")
     ap.add_argument("--oracle-worker", nargs=2, type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--probe", choices=["apply", "solve"], default=None,
+                    help="run one kernel-level driver (see the module docstring) instead of the benchmark")
+    ap.add_argument("--n", type=int, default=40, help="probe: cube of n^3 hexes x 6 tets")
+    ap.add_argument("--reps", type=int, default=3, help="probe: timed repetitions after one warm-up")
+    ap.add_argument("--vec", choices=["f32", "f64"], default="f32", help="probe apply: vector type")
+    ap.add_argument("--kind", choices=["linear", "nh"], default="linear", help="probe apply: material")
+    ap.add_argument("--op", choices=["tangent", "residual"], default="tangent", help="probe apply: operator")
+    ap.add_argument("--max-iter", type=int, default=100000, help="probe solve: PCG iteration cap")
     args = ap.parse_args()
     if args.oracle_worker is not None:
         print(json.dumps(cpu_oracle_warm_solve(tuple(args.oracle_worker))))
         return 0
+    if args.probe is not None:
+        return probe(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -629,6 +648,55 @@ def _newton(P, pi, torch):
     out["workload"] = "NH bar 64x16x16 hexes x 6 = 98,304 tets, 20% stretch, tol 1e-8, inner PCG 1e-8"
     mesh.close()
     return out
+
+
+def probe(a):
+    """Kernel-level driver for profilers: one warm-up call, then a.reps timed calls."""
+    import torch
+
+    import pfem_inputs as pi
+    import paper_2601_03086_gb300 as P
+    from paper_2601_03086_gb300 import build
+
+    build.build()
+    p = pi.cube_problem(a.n, seed=2) if a.kind == "linear" else pi.bar_problem(4 * a.n, a.n, a.n, seed=3)
+    mesh = P.Mesh(p)
+    out = {"probe": a.probe, "n": a.n, "stats": mesh.stats()}
+    ev = _events(torch)
+    if a.probe == "apply":
+        dt = torch.float32 if a.vec == "f32" else torch.float64
+        v = torch.randn(mesh.n_dofs, device="cuda", dtype=dt)
+        u = 0.01 * torch.randn_like(v) if (a.kind == "nh" or a.op == "residual") else None
+        y = torch.empty_like(v)
+        arith = "f32" if a.vec == "f64" else None
+
+        def op():
+            if a.op == "tangent":
+                P.pfem_tangent_apply(mesh, u, v, y, arith=arith)
+            else:
+                P.pfem_residual(mesh, u, y, arith=arith)
+
+        op()
+        ev[0].record()
+        for _ in range(a.reps):
+            op()
+        ev[1].record()
+        ev[1].synchronize()
+        out.update({"apply_us": ev[0].elapsed_time(ev[1]) * 1e3 / a.reps, "op": a.op})
+    else:
+        P.pfem_set_solver_mode(MODES[a.solver_mode])
+        P.pfem_solve_linear(mesh, tol=TOL, max_iter=a.max_iter, raise_on_error=False)
+        ev[0].record()
+        for _ in range(a.reps):
+            _, info = P.pfem_solve_linear(mesh, tol=TOL, max_iter=a.max_iter, raise_on_error=False)
+        ev[1].record()
+        ev[1].synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / a.reps
+        out.update({"solve_ms": ms, "iterations": info["iterations"], "solver_mode": a.solver_mode,
+                    "us_per_iteration": 1e3 * ms / max(info["iterations"], 1)})
+    print(json.dumps(out))
+    mesh.close()
+    return 0
 
 
 def _cpu_baseline():

@@ -7,12 +7,14 @@
  * and drives Jacobi-PCG and Newton-Krylov solves started from a caller-supplied guess.
  *
  * Paper: "Pretrained Finite Element Method" (PFEM, arXiv 2601.03086).
- *   - energy loss, linear:       Sec. 3.1, Eq. of the plate loss (Psi = 1/2 sigma:eps)
- *   - energy loss, Neo-Hookean:  Sec. 3.2 (Psi = 1/2 lam ln^2 J - mu ln J + 1/2 mu (I1 - d))
+ *   - energy loss, linear:       Sec. "Linear elastic plate with arbitrary holes" (plate
+ *                                loss, Psi = 1/2 sigma:eps)
+ *   - energy loss, Neo-Hookean:  Sec. "Nonlinear hyperelasticity" (Psi = 1/2 lam ln^2 J
+ *                                - mu ln J + 1/2 mu (I1 - d))
  *   - explicit FE derivatives:   App. A (shape-function differentiation)
  *   - f_int, f_ext, tangent:     App. B (principle of virtual power, total Lagrangian,
  *                                K = K_geo + K_mat, Newton-Raphson with load steps)
- *   - warm start + criterion:    Sec. 2.3.2 (U^(0) = U^NO, ||r|| < tol, skip test)
+ *   - warm start + criterion:    Sec. "Warm-start" (U^(0) = U^NO, ||r|| < tol, skip test)
  *
  * Conventions shared by every entry point
  *   - Node vectors (u, v, y, r, ...) are device pointers, DOF-interleaved: entry
@@ -63,8 +65,8 @@ typedef struct pfem_mesh_s* pfem_mesh_t;
 typedef struct pfem_batch_s* pfem_batch_t;
 typedef struct pfem_server_s* pfem_server_t;
 
-/* Problem description (Sec. 2.3.1 point-cloud inputs: geometry, material, boundary
- * conditions). All pointers are HOST pointers, read during pfem_mesh_create only. */
+/* Problem description (the point-cloud inputs of Sec. "Input and output of neural
+ * operators": geometry, material, boundary conditions). All pointers are HOST pointers, read during pfem_mesh_create only. */
 typedef struct {
   int32_t dim;                     /* 2: P1 triangles, plane strain, unit thickness; 3: P1 tets */
   int64_t n_nodes;                 /* >= 1 */
@@ -103,7 +105,7 @@ typedef struct {
   int32_t inverted_backtracks;     /* Newton step halvings caused by J <= 0 */
   double rel_residual_recursive;   /* ||r_k|| / ref as tracked by the iteration */
   double rel_residual_true_f64;    /* ||P(f_ext - f_int(u))|| / ref with the FP64 operator */
-  double initial_rel_residual;     /* ||r(u0)|| / ref, the Sec. 2.3.2 skip-test quantity */
+  double initial_rel_residual;     /* ||r(u0)|| / ref, the Sec. "Warm-start" skip-test quantity */
   double reference_norm;           /* ref = ||r(u_lift)||: zero free DOFs, prescribed values */
   pfem_status status;
   int64_t kernel_launches;         /* kernels this solve ran (graph replays included) */
@@ -135,7 +137,8 @@ pfem_status pfem_mesh_stats_get(pfem_mesh_t mesh, pfem_mesh_stats* out);
  * multiplied by s in every later call. Default 1. */
 pfem_status pfem_mesh_set_load_scale(pfem_mesh_t mesh, double s);
 
-/* ---- element operator (Sec. 3.1/3.2 energies; App. B forces and tangent) ----------- */
+/* ---- element operator (energies of Secs. "Linear elastic plate with arbitrary holes" and
+ *      "Nonlinear hyperelasticity"; App. B forces and tangent) -------------------------- */
 
 /* Pi(u) = sum_e V_e Psi_e(u) - s f_ext . u and the strain part sum_e V_e Psi_e(u).
  * u: n_dofs device vector (dtype). Results are written to HOST doubles (either may be
@@ -158,13 +161,14 @@ pfem_status pfem_tangent_apply(pfem_mesh_t mesh, pfem_dtype dtype, const void* u
  * they apply the operator (a frozen or exhausted memory pool, code running inside allocator
  * callbacks, runtimes that only own memory handed to them up front). The paper has no
  * counterpart: this is a library convenience. The call allocates nothing; the per-call
- * scratch of the element-tile pass (halo partial sums) lives in a fixed 16 MiB device array
- * that every GPU loading the library holds until exit. Limits and behaviour:
- *   - meshes whose halo scratch (n_partials * dim * 4 bytes for F32/F64_F32, * 8 for F64)
- *     exceeds 16 MiB are rejected with PFEM_ERR_INVALID_ARG;
+ * scratch of the element-tile pass (halo partial sums) lives in a fixed 16 MiB device array.
+ * The array is created on a device when the first mesh is created there (pfem_mesh_create
+ * looks its address up, which loads its module), never by this call, and the device then
+ * holds it until the process exits. Limits and behaviour:
+ *   - meshes whose halo scratch (n_partials * 4 * 4 bytes for F32/F64_F32, * 4 * 8 for F64:
+ *     at most 1,048,576 partials in FP32 arithmetic and 524,288 in FP64) exceeds 16 MiB are
+ *     rejected with PFEM_ERR_INVALID_ARG;
  *   - the current device must be the mesh's device (else PFEM_ERR_INVALID_ARG);
- *   - the first call on a device looks the array's device address up (set-up); make that
- *     first call before any stream capture;
  *   - every call shares the one array and it keeps the last call's contents (each call
  *     overwrites what it reads, so nothing needs clearing); calls that overlap on the GPU,
  *     on any stream, race on it and must be serialised by the caller.
@@ -172,11 +176,30 @@ pfem_status pfem_tangent_apply(pfem_mesh_t mesh, pfem_dtype dtype, const void* u
 pfem_status pfem_tangent_apply_noalloc(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, const void* v,
                                        void* y);
 
+/* Derivatives of the energy loss for reverse-mode differentiation (the backward pass of the
+ * physics loss of Sec. "Pretraining"; App. A explicit derivatives), with the upstream
+ * factor applied inside the kernel. scale: a device scalar of the vector type
+ * (float for PFEM_F32, double otherwise), NULL = 1.
+ *   pfem_energy_gradient:  g = scale * P (f_int(u) - s f_ext)   (dPi/du on free DOFs, 0 on
+ *                          prescribed DOFs; the same values as pfem_residual when scale = 1)
+ *   pfem_energy_hvp:       y = scale * P K(u) P v                (Hessian of Pi on the free DOFs
+ *                          times v; rows and columns of prescribed DOFs are zero, unlike the
+ *                          identity block of pfem_tangent_apply)
+ * u, v, g, y: n_dofs device vectors of dtype. Asynchronous. */
+pfem_status pfem_energy_gradient(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, const void* scale, void* g);
+pfem_status pfem_energy_hvp(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, const void* v, const void* scale,
+                            void* y);
+
+/* out = a . b over the mesh's n_dofs entries (device vectors of dtype), summed in FP64 in a
+ * fixed order and written to the device scalar out in the vector type (the chain-rule term of
+ * the upstream factor in the energy loss's double backward). Asynchronous. */
+pfem_status pfem_dot(pfem_mesh_t mesh, pfem_dtype dtype, const void* a, const void* b, void* out);
+
 /* d = diag A(u): diag K(u) on free DOFs, 1 on Dirichlet DOFs (the Jacobi preconditioner).
  * u ignored for linear material. Asynchronous. */
 pfem_status pfem_jacobi_diag(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, void* d);
 
-/* ---- warm-started solvers (Sec. 2.3.2; App. B) ------------------------------------- */
+/* ---- warm-started solvers (Sec. "Warm-start"; App. B) ------------------------------ */
 
 /* Linear elasticity K U = F by Jacobi-PCG started from u0 (NULL = zero). The prescribed
  * values overwrite u0 on Dirichlet DOFs. Stops when ||r_k|| / ref < tol with
@@ -211,6 +234,16 @@ pfem_status pfem_solve_newton(pfem_mesh_t mesh, pfem_dtype dtype, const double* 
  * loop. Other values: PFEM_ERR_INVALID_ARG. */
 pfem_status pfem_set_solver_mode(int32_t mode);
 
+/* Failure-detection settings of the persistent solver mode (process-wide; the default is
+ * spin_limit <= 0, absent_cta = -1). Every grid-barrier wait of the persistent PCG kernel polls
+ * at most spin_limit times (each poll sleeps >= 32 ns; the default allows more than a second)
+ * and then flags the barrier, so the solve ends with PFEM_ERR_TIMEOUT and the context stays
+ * usable. absent_cta >= 0 makes that CTA of later persistent launches leave at its first grid
+ * barrier without arriving, as a CTA that never arrives would, so that tests can make the
+ * other CTAs' waits run out (host-side injection; nothing faults or hangs). absent_cta < -1:
+ * PFEM_ERR_INVALID_ARG. The paper has no counterpart. */
+pfem_status pfem_set_barrier_test(int64_t spin_limit, int32_t absent_cta);
+
 /* Per-kernel timing of later solves (process-wide; 1 = on, 0 = off, the default; other
  * values PFEM_ERR_INVALID_ARG). While on, the plain loop (solver mode 1) brackets the two
  * kernels of every PCG iteration with CUDA events on the mesh's stream and reports their
@@ -220,7 +253,8 @@ pfem_status pfem_set_kernel_timing(int32_t on);
 
 /* ---- ragged batch: energy loss, gradient and Hessian-vector product in one launch --- */
 
-/* The differentiable FE energy loss of Sec. 3.1/3.2 over several meshes at once (the
+/* The differentiable FE energy loss of Secs. "Linear elastic plate with arbitrary holes"
+ * and "Nonlinear hyperelasticity" over several meshes at once (the
  * pretraining loss is summed over a batch of geometries). Groups 3-D meshes (one device;
  * materials may differ per mesh) for one-launch evaluation. The meshes must outlive the
  * batch; a batch evaluation uses the meshes' scratch, so it must not overlap on the GPU with
@@ -248,7 +282,7 @@ pfem_status pfem_batch_eval(pfem_batch_t batch, const float* u, const float* v, 
 typedef enum { PFEM_SOLVE_LINEAR = 0, PFEM_SOLVE_NEWTON = 1 } pfem_solve_kind;
 
 /* A server owns planner threads, one worker thread and a CUDA stream on the device current
- * at creation (Sec. 2.3.2: problems arrive at a platform whose FE iterations refine each
+ * at creation (Sec. "Warm-start": problems arrive at a platform whose FE iterations refine each
  * warm start). Requests are planned on the host as they arrive, admitted in arrival order
  * while a slot is free and their device footprint (mesh plan + solver vectors) fits
  * hbm_budget_bytes, and then every resident solve advances in shared launches (one fused

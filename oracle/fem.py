@@ -8,11 +8,11 @@ Every routine is vectorised over elements with numpy but keeps the paper's formu
   * explicit shape-function differentiation of P1 simplices (App. A; App. B interpolation
     X_i = N_I X_iI, u_i = N_I u_iI);
   * linear elasticity: eps = sym grad u, sigma = E/(1+nu) eps + E nu/((1+nu)(1-2nu)) tr(eps) I,
-    Psi = 1/2 sigma:eps (Sec. 3.1 energy loss); element stiffness assembled in Voigt form
+    Psi = 1/2 sigma:eps (Sec. "Linear elastic plate with arbitrary holes" energy loss); element stiffness assembled in Voigt form
     K_e = V B^T D B (App. B, f_int = K u in linear FEM);
-  * compressible Neo-Hookean (Sec. 3.2 energy loss): Psi = 1/2 lam (ln J)^2 - mu ln J +
+  * compressible Neo-Hookean (Sec. "Nonlinear hyperelasticity" energy loss): Psi = 1/2 lam (ln J)^2 - mu ln J +
     1/2 mu (I1 - d), with I1 = tr C, C = F^T F, F = I + grad u; Lame parameters from (E, nu)
-    by the Sec. 3.2 formula. Total-Lagrangian internal force f_iI = int dN_I/dX_l F_ik S_kl
+    by the Sec. "Nonlinear hyperelasticity" formula. Total-Lagrangian internal force f_iI = int dN_I/dX_l F_ik S_kl
     (App. B) with S = 2 dPsi/dC = mu (I - C^-1) + lam ln J C^-1, and tangent
     K = K_geo + K_mat, K_geo = int G0^T S G0, K_mat = int B0^T C^SE B0 (App. B) with
     C^SE = 2 dS/dC = lam C^-1 (x) C^-1 + (mu - lam ln J)(C^-1_ik C^-1_jl + C^-1_il C^-1_jk);
@@ -56,7 +56,7 @@ def shape_gradients(Xe):
 
 
 def lame(E, nu):
-    """Lame parameters from Young's modulus and Poisson's ratio (Sec. 3.2)."""
+    """Lame parameters from Young's modulus and Poisson's ratio (Sec. "Linear elastic plate with arbitrary holes")."""
     lam = nu * E / ((1.0 + nu) * (1.0 - 2.0 * nu))
     mu = E / (2.0 * (1.0 + nu))
     return mu, lam
@@ -141,12 +141,12 @@ def _assemble(mesh, Ke):
 
 
 # ---------------------------------------------------------------------------------------
-# Linear elasticity (Sec. 3.1 energy loss; App. B with f_int = K u)
+# Linear elasticity (Sec. "Linear elastic plate with arbitrary holes" energy loss; App. B with f_int = K u)
 # ---------------------------------------------------------------------------------------
 
 
 def linear_stress(eps, E, nu):
-    """sigma = E/(1+nu) eps + E nu/((1+nu)(1-2nu)) tr(eps) I (Sec. 3.1)."""
+    """sigma = E/(1+nu) eps + E nu/((1+nu)(1-2nu)) tr(eps) I (Sec. "Linear elastic plate with arbitrary holes")."""
     d = eps.shape[-1]
     tr = np.trace(eps, axis1=-2, axis2=-1)
     return (E / (1.0 + nu))[:, None, None] * eps + (E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu)) * tr)[:, None, None] * np.eye(d)
@@ -213,7 +213,7 @@ def assemble_linear_K(mesh):
 
 
 # ---------------------------------------------------------------------------------------
-# Compressible Neo-Hookean (Sec. 3.2 energy loss; App. B total Lagrangian)
+# Compressible Neo-Hookean (Sec. "Nonlinear hyperelasticity" energy loss; App. B total Lagrangian)
 # ---------------------------------------------------------------------------------------
 
 
@@ -314,7 +314,8 @@ def strain_energy(mesh, u):
 
 
 def total_energy(mesh, u, scale=1.0):
-    """Pi(u) = sum_e V_e Psi_e - f_ext . u (energy loss of Sec. 3.1/3.2 on the FE space)."""
+    """Pi(u) = sum_e V_e Psi_e - f_ext . u (energy losses of the plate and
+    hyperelasticity results on the FE space)."""
     return strain_energy(mesh, u) - float(external_force(mesh, scale) @ np.asarray(u).reshape(-1))
 
 

@@ -6,8 +6,8 @@ TEST INFRASTRUCTURE (see oracle/fem.py): never imported by the product path.
     Dirichlet DOFs are eliminated (K_ff u_f = f_f - K_fc u_c); the reference norm is the
     residual of the lifted start (zero free DOFs, prescribed values on Dirichlet DOFs),
     which equals ||f_f|| when the prescribed values are zero and does not depend on u0.
-  * Warm start: the iteration starts from U^(0) = U^NO instead of zero (Sec. 2.3.2, the
-    iteration U^(k+1) = phi(U^(k); K, F, U^(0) = U^NO)); the skip test of Sec. 2.3.2 is the
+  * Warm start: the iteration starts from U^(0) = U^NO instead of zero (Sec. "Warm-start", the
+    iteration U^(k+1) = phi(U^(k); K, F, U^(0) = U^NO)); the skip test of Sec. "Warm-start" is the
     k = 0 check of the same criterion.
   * Jacobi-PCG: the preconditioned conjugate gradient method with M = diag(K_ff) (the
     paper uses "PCG" without naming the preconditioner; Jacobi is this build's reading).

@@ -20,13 +20,17 @@ from .api import (  # noqa: F401
     pfem_batch_destroy,
     pfem_batch_eval,
     pfem_batch_offsets,
+    pfem_dot,
     pfem_energy,
+    pfem_energy_gradient,
+    pfem_energy_hvp,
     pfem_jacobi_diag,
     pfem_mesh_create,
     pfem_mesh_destroy,
     pfem_mesh_set_load_scale,
     pfem_plan_check,
     pfem_residual,
+    pfem_set_barrier_test,
     pfem_set_kernel_timing,
     pfem_set_solver_mode,
     pfem_solve_linear,

@@ -96,12 +96,16 @@ SIGNATURES = {
     "pfem_tangent_apply": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pfem_tangent_apply_noalloc": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pfem_jacobi_diag": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "pfem_energy_gradient": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pfem_energy_hvp": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "pfem_dot": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "pfem_solve_linear": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
                                       C.POINTER(SolveInfo)]),
     "pfem_solve_newton": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_int32,
                                       C.c_double, C.c_void_p, C.POINTER(SolveInfo)]),
     "pfem_set_solver_mode": (C.c_int32, [C.c_int32]),
     "pfem_set_kernel_timing": (C.c_int32, [C.c_int32]),
+    "pfem_set_barrier_test": (C.c_int32, [C.c_int64, C.c_int32]),
     "pfem_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     "pfem_batch_destroy": (None, [C.c_void_p]),
     "pfem_batch_offsets": (C.c_int32, [C.c_void_p, C.POINTER(C.c_int64)]),

@@ -98,7 +98,6 @@ class Mesh:
         self.n_nodes = int(desc.n_nodes)
         self.n_elems = int(desc.n_elems)
         self.n_dofs = self.n_nodes * dim
-        self.free_mask = (np.asarray(problem["dirichlet_mask"]).reshape(-1) == 0).astype(np.float64)
         self._arrays = None
 
     def stats(self):
@@ -151,6 +150,40 @@ def pfem_tangent_apply(mesh, u, v, y=None, arith=None):
     return y
 
 
+def _scalar(s, like, name):
+    """Device pointer of a one-entry tensor of the vector type (None = 1)."""
+    if s is None:
+        return None
+    if not isinstance(s, torch.Tensor) or not s.is_cuda or s.numel() != 1 or s.dtype != like.dtype:
+        raise TypeError("%s must be a one-entry CUDA tensor of dtype %s" % (name, like.dtype))
+    return C.c_void_p(s.contiguous().data_ptr())
+
+
+def pfem_energy_gradient(mesh, u, scale=None, g=None, arith=None):
+    """g = scale * P (f_int(u) - f_ext), the upstream factor applied in the kernel."""
+    g = torch.empty_like(u) if g is None else g
+    check(lib().pfem_energy_gradient(mesh.handle, _dtype_of(u, arith), _dev(u, mesh.n_dofs, "u"),
+                                     _scalar(scale, u, "scale"), _dev(g, mesh.n_dofs, "g")))
+    return g
+
+
+def pfem_energy_hvp(mesh, u, v, scale=None, y=None, arith=None):
+    """y = scale * P K(u) P v (zero rows and columns on prescribed DOFs)."""
+    y = torch.empty_like(v) if y is None else y
+    up = _dev(u, mesh.n_dofs, "u") if u is not None else None
+    check(lib().pfem_energy_hvp(mesh.handle, _dtype_of(v, arith), up, _dev(v, mesh.n_dofs, "v"),
+                                _scalar(scale, v, "scale"), _dev(y, mesh.n_dofs, "y")))
+    return y
+
+
+def pfem_dot(mesh, a, b, out=None):
+    """a . b as a 0-dim device tensor of the vectors' dtype (FP64 sums, fixed order)."""
+    out = torch.empty((), dtype=a.dtype, device=a.device) if out is None else out
+    check(lib().pfem_dot(mesh.handle, _dtype_of(a), _dev(a, mesh.n_dofs, "a"), _dev(b, mesh.n_dofs, "b"),
+                         C.c_void_p(out.data_ptr())))
+    return out
+
+
 def pfem_jacobi_diag(mesh, u=None, d=None, dtype=torch.float32, arith=None):
     if d is None:
         d = torch.empty(mesh.n_dofs, dtype=u.dtype if u is not None else dtype, device="cuda")
@@ -192,6 +225,10 @@ def pfem_solve_newton(mesh, u0=None, tol=1e-8, n_load_steps=1, max_newton=50, in
 
 def pfem_set_solver_mode(mode):
     check(lib().pfem_set_solver_mode(int(mode)))
+
+
+def pfem_set_barrier_test(spin_limit=0, absent_cta=-1):
+    check(lib().pfem_set_barrier_test(int(spin_limit), int(absent_cta)))
 
 
 def pfem_set_kernel_timing(on):
@@ -309,27 +346,25 @@ def batch_energy(u, batch):
 
 
 class _MeshGrad(torch.autograd.Function):
+    """g = s dPi/du (gradient kernel, s applied in the kernel); its backward is the Hessian
+    action (scaled in the kernel) and, for s, the unscaled gradient dotted with the upstream
+    vector (dot kernel)."""
+
     @staticmethod
-    def forward(ctx, u, mesh):
-        ctx.save_for_backward(u)
+    def forward(ctx, u, s, mesh):
+        ctx.save_for_backward(u, s)
         ctx.mesh = mesh
-        return pfem_residual(ctx.mesh, u)
+        return pfem_energy_gradient(mesh, u, scale=s)
 
     @staticmethod
     def backward(ctx, w):
-        (u,) = ctx.saved_tensors
-        # Hessian of the energy on free DOFs: the kernel reads w as 0 on prescribed DOFs and
-        # returns the identity block there, which the free-DOF mask removes
-        y = pfem_tangent_apply(ctx.mesh, u, w.contiguous())
-        return _zero_prescribed(ctx.mesh, y), None
-
-
-def _zero_prescribed(mesh, y):
-    m = getattr(mesh, "_free_mask", None)
-    if m is None or m.device != y.device or m.dtype != y.dtype:
-        m = torch.as_tensor(mesh.free_mask, dtype=y.dtype, device=y.device)
-        mesh._free_mask = m
-    return y * m
+        u, s = ctx.saved_tensors
+        w = w.contiguous()
+        hv = pfem_energy_hvp(ctx.mesh, u, w, scale=s)
+        ds = None
+        if ctx.needs_input_grad[1]:
+            ds = pfem_dot(ctx.mesh, pfem_energy_gradient(ctx.mesh, u), w)
+        return hv, ds, None
 
 
 class _MeshEnergy(torch.autograd.Function):
@@ -343,7 +378,7 @@ class _MeshEnergy(torch.autograd.Function):
     @staticmethod
     def backward(ctx, ge):
         (u,) = ctx.saved_tensors
-        return _MeshGrad.apply(u, ctx.mesh) * ge, None
+        return _MeshGrad.apply(u, ge.contiguous(), ctx.mesh), None
 
 
 def mesh_energy(u, mesh):

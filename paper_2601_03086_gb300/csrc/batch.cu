@@ -1,5 +1,7 @@
 // Ragged batches: several meshes' energies, gradients and Hessian-vector products in one
-// element launch (the differentiable FE energy loss of Sec. 3.1/3.2 over a batch).
+// element launch (the differentiable FE energy loss of the plate and
+// hyperelasticity results, Secs. "Linear elastic plate with arbitrary holes" and "Nonlinear
+// hyperelasticity", over a batch).
 
 #include <cstring>
 #include <new>

@@ -60,7 +60,15 @@ pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem
   if (const char* env = std::getenv("PFEM_TILE_ELEMS")) tile_elems = std::atoi(env);
   pfem_status st = build_plan(desc, &hp, &fext, tile_elems);
   if (st != PFEM_OK) return st;
-  return mesh_upload(hp, fext, desc, static_cast<cudaStream_t>(cuda_stream), out);
+  if ((st = mesh_upload(hp, fext, desc, static_cast<cudaStream_t>(cuda_stream), out))) return st;
+  // the allocation-free apply's scratch array is created here, on the mesh's device, so that
+  // pfem_tangent_apply_noalloc never triggers the (lazy) load of its module itself
+  void* scratch = nullptr;
+  if ((st = noalloc_scratch(&scratch))) {
+    pfem_mesh_destroy(*out);
+    *out = nullptr;
+  }
+  return st;
 }
 
 }  // extern "C"
@@ -384,6 +392,42 @@ pfem_status pfem_tangent_apply(pfem_mesh_t m, pfem_dtype dt, const void* u, cons
   }
   OpArgs a{u, v, y, nullptr, nullptr, m->load_scale};
   return launch_element_op(m->plan, OP_TANGENT, vt_of(dt), ct_of(dt), a, m->stream);
+}
+
+pfem_status pfem_energy_gradient(pfem_mesh_t m, pfem_dtype dt, const void* u, const void* scale, void* g) {
+  pfem_status st = op_common(m, dt);
+  if (st) return st;
+  if (!u || !g) {
+    set_error("u/g is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  OpArgs a{u, nullptr, nullptr, g, nullptr, m->load_scale};
+  a.out_scale = scale;
+  return launch_element_op(m->plan, OP_RESIDUAL, vt_of(dt), ct_of(dt), a, m->stream);
+}
+
+pfem_status pfem_energy_hvp(pfem_mesh_t m, pfem_dtype dt, const void* u, const void* v, const void* scale,
+                            void* y) {
+  pfem_status st = op_common(m, dt);
+  if (st) return st;
+  if (!v || !y || (m->plan.kind == PFEM_NEOHOOKEAN && !u)) {
+    set_error("u/v/y is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  OpArgs a{u, v, y, nullptr, nullptr, m->load_scale};
+  a.out_scale = scale;
+  a.hess = 1;  // rows and columns of prescribed DOFs are zero
+  return launch_element_op(m->plan, OP_TANGENT, vt_of(dt), ct_of(dt), a, m->stream);
+}
+
+pfem_status pfem_dot(pfem_mesh_t m, pfem_dtype dt, const void* a, const void* b, void* out) {
+  pfem_status st = op_common(m, dt);
+  if (st) return st;
+  if (!a || !b || !out) {
+    set_error("a/b/out is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  return vk_dot(m->n_dofs, vt_of(dt), a, b, out, m->red_partials, m->red_counter, m->stream);
 }
 
 pfem_status pfem_jacobi_diag(pfem_mesh_t m, pfem_dtype dt, const void* u, void* d) {

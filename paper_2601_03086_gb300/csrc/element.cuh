@@ -7,9 +7,9 @@
 //     grad w = G'/det with G' = sum_a (w_a - w_0) (x) c_a, and for a stress T,
 //     V T dN_a = T c_a * sgn(det)/d!  (and V (T(G'/det)) dN_a = T(G') c_a / (d! |det|) when T
 //     is linear in the gradient).
-//   linear (Sec. 3.1): eps = sym grad w, sigma = 2 mu eps + lam tr(eps) I, Psi = 1/2 sigma:eps;
+//   linear (Sec. "Linear elastic plate with arbitrary holes"): eps = sym grad w, sigma = 2 mu eps + lam tr(eps) I, Psi = 1/2 sigma:eps;
 //     force / tangent action  y_a = V sigma(w) dN_a  (f_int = K u for linear FEM, App. B)
-//   Neo-Hookean (Sec. 3.2 energy; App. B total Lagrangian): F = I + grad u, J = det F,
+//   Neo-Hookean (Sec. "Nonlinear hyperelasticity" energy; App. B total Lagrangian): F = I + grad u, J = det F,
 //     H = F^-T = cof(F) / J, first Piola-Kirchhoff stress P = F S = mu (F - H) + lam ln J H
 //     (S = mu (I - C^-1) + lam ln J C^-1), f_a = V P dN_a,
 //     Psi = 1/2 lam ln^2 J - mu ln J + 1/2 mu (I1 - d);

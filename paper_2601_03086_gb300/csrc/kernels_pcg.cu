@@ -1,4 +1,4 @@
-// Persistent Jacobi-PCG kernel (App. B linear system, Sec. 2.3.2 warm start): one cooperative
+// Persistent Jacobi-PCG kernel (App. B linear system, Sec. "Warm-start"): one cooperative
 // launch keeps every CTA resident and runs whole iterations of the two-kernel body of the
 // graph mode, with grid barriers where the graph has kernel boundaries:
 //
@@ -23,11 +23,9 @@
 
 namespace pfem {
 
-constexpr long long kBarrierSpinLimit = 1ll << 25;  // x >= 32 ns sleep: more than a second
-
 // Grid-wide barrier among co-resident CTAs; returns false (in every thread) once any CTA has
 // given up waiting. `gen` is thread 0's count of completed barriers.
-__device__ __forceinline__ bool grid_barrier(GridBar* b, unsigned int& gen, int* s_flag) {
+__device__ __forceinline__ bool grid_barrier(GridBar* b, unsigned int& gen, int* s_flag, long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     cuda::atomic_ref<unsigned int, cuda::thread_scope_device> cnt(b->count);
@@ -41,7 +39,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, unsigned int& gen, int*
     } else {
       long long spins = 0;
       while (g.load(cuda::memory_order_acquire) == gen) {
-        if (err.load(cuda::memory_order_relaxed) != 0 || ++spins > kBarrierSpinLimit) {
+        if (err.load(cuda::memory_order_relaxed) != 0 || ++spins > limit) {
           err.store(1, cuda::memory_order_relaxed);
           bad = 1;
           break;
@@ -107,7 +105,10 @@ __global__ void __launch_bounds__(kThreads, 2) pcg_persistent_kernel(DevPlan P, 
       process_tile<DIM, KIND, OPS, double, float>(P, oa, t, smem, L);
       __syncthreads();
     }
-    if (!(ok = grid_barrier(A.bar, gen, &s_flag))) break;
+    // failure-detection test: one CTA leaves without arriving (after its tiles, so the
+    // apply's tile ticket is complete); every other CTA's wait runs out
+    if ((int)blockIdx.x == A.absent_cta) return;
+    if (!(ok = grid_barrier(A.bar, gen, &s_flag, A.spin_limit))) break;
     if (threadIdx.x == 0) {
       s_stop = __ldcg(&st->done) != 0 ? 1 : 0;
       s_alpha = __ldcg(&st->alpha);
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(kThreads, 2) pcg_persistent_kernel(DevPlan P, 
           pcg_finish_update(st, v[0], v[1]);
       }
     }
-    if (!(ok = grid_barrier(A.bar, gen, &s_flag))) break;
+    if (!(ok = grid_barrier(A.bar, gen, &s_flag, A.spin_limit))) break;
     if (threadIdx.x == 0) read_state();
     __syncthreads();
     if (s_stop) break;

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(256) halo_finish_kernel(DevPlan P, OpArgs A, i
   const int h = blockIdx.x * blockDim.x + threadIdx.x;
   if (h >= P.n_halo) return;
   const CT* part = static_cast<const CT*>(P.partial) + (size_t)region * P.n_partials * 4;
-  const CT sc = A.out_scale ? CT(*A.out_scale) : CT(1);
+  const CT sc = A.out_scale ? CT(*static_cast<const VT*>(A.out_scale)) : CT(1);
   const int4 rec = P.halo_node[h];
   CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
   for (int k = rec.x; k < rec.x + rec.y; ++k) {

@@ -180,6 +180,17 @@ __global__ void __launch_bounds__(kReduceThreads)
   if (grid_sum<1>(a, partials, counter, scratch) && threadIdx.x == 0) *out = sqrt(a[0]);
 }
 
+// a . b over n entries (FP64 sums of the products), written to out in the vector type
+template <typename VT>
+__global__ void __launch_bounds__(kReduceThreads)
+    dot_kernel(int64_t n, const VT* a, const VT* b, VT* out, double* partials, unsigned int* counter) {
+  __shared__ double scratch[8];
+  double s[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s[0] += (double)a[i] * (double)b[i];
+  if (grid_sum<1>(s, partials, counter, scratch) && threadIdx.x == 0) *out = VT(s[0]);
+}
+
 __global__ void axpy_kernel(int64_t n, double a, const double* x, double* y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] += a * x[i];
@@ -226,6 +237,21 @@ pfem_status vk_replace(int64_t n, const double* res, double* r, const double* di
 pfem_status vk_norm2(int64_t n, const double* v, double* out, double* partials, unsigned int* counter,
                      cudaStream_t s) {
   norm2_kernel<<<kReduceBlocks, kReduceThreads, 0, s>>>(n, v, out, partials, counter); PFEM_COUNT_LAUNCH();
+  PFEM_CUDA(cudaGetLastError());
+  return PFEM_OK;
+}
+
+pfem_status vk_dot(int64_t n, pfem_dtype vt, const void* a, const void* b, void* out, double* partials,
+                   unsigned int* counter, cudaStream_t s) {
+  if (vt == PFEM_F32)
+    dot_kernel<float><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, static_cast<const float*>(a),
+                                                              static_cast<const float*>(b), static_cast<float*>(out),
+                                                              partials, counter);
+  else
+    dot_kernel<double><<<kReduceBlocks, kReduceThreads, 0, s>>>(n, static_cast<const double*>(a),
+                                                               static_cast<const double*>(b), static_cast<double*>(out),
+                                                               partials, counter);
+  PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   return PFEM_OK;
 }

@@ -18,5 +18,8 @@ pfem_status vk_replace(int64_t n, const double* res, double* r, const double* di
 pfem_status vk_norm2(int64_t n, const double* v, double* out, double* partials, unsigned int* counter,
                      cudaStream_t s);
 pfem_status vk_axpy(int64_t n, double a, const double* x, double* y, cudaStream_t s);
+// out = a . b (vector type vt, FP64 sums), deterministic
+pfem_status vk_dot(int64_t n, pfem_dtype vt, const void* a, const void* b, void* out, double* partials,
+                   unsigned int* counter, cudaStream_t s);
 
 }  // namespace pfem

@@ -26,8 +26,10 @@ void* g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device. The host-side name of the
 // array is only a stand-in, so the address is looked up once per device with that device
-// current (cudaGetSymbolAddress) and cached.
-static pfem_status noalloc_scratch(void** out) {
+// current (cudaGetSymbolAddress) and cached. With lazy module loading the first lookup also
+// loads this file's module, which is when the driver allocates the array: pfem_mesh_create
+// calls this (allocation is allowed there), so the no-alloc call itself only reads the cache.
+pfem_status noalloc_scratch(void** out) {
   int dev = -1;
   PFEM_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) {
@@ -77,7 +79,7 @@ extern "C" pfem_status pfem_tangent_apply_noalloc(pfem_mesh_t m, pfem_dtype dt, 
               kNoAllocScratchBytes);
     return PFEM_ERR_INVALID_ARG;
   }
-  void* scratch = nullptr;
+  void* scratch = nullptr;  // resolved when the mesh was created on this device
   pfem_status st = noalloc_scratch(&scratch);
   if (st != PFEM_OK) return st;
   DevPlan P = m->plan;  // same plan, scratch redirected to the fixed array

@@ -245,7 +245,13 @@ struct PersistArgs {
   unsigned int* red_counter;  // last-block ticket of the update (zero; reset by its user)
   GridBar* bar;
   int64_t n;            // DOFs
+  long long spin_limit; // polls of a grid-barrier wait before it gives up (each >= 32 ns)
+  int absent_cta;       // failure-detection test: this CTA leaves at its first grid barrier
+                        // without arriving (-1 = none), so the others' waits run out
 };
+
+// Default and test settings of the persistent kernel's barrier waits (solve.cu).
+constexpr long long kBarrierSpinLimit = 1ll << 25;  // x >= 32 ns sleep: more than a second
 
 struct OpArgs {
   const void* u;    // VT*, may be null for linear tangent/diag
@@ -255,7 +261,8 @@ struct OpArgs {
   void* d;          // VT* diagonal output
   double load_scale;
   PcgArgs pcg;      // OP_PCG only
-  const float* out_scale;  // device scalar multiplying residual / tangent outputs (null = 1)
+  const void* out_scale;   // device scalar of the vector type multiplying residual / tangent
+                           // outputs (null = 1)
   int hess;                // tangent on prescribed DOFs: 0 = identity block (y = v), 1 = zero
   int defer_halo;          // 1: tiles publish halo partials in tile order (no loads, no tickets);
                            // halo_finish_kernel completes them
@@ -346,6 +353,10 @@ pfem_status launch_pcg_persistent(const DevPlan& P, pfem_dtype ct, const Persist
 // Halo partials from which launch_element_op completes halo nodes in a separate pass instead
 // of inside the tiles (removes the per-tile fence / ticket / reload chain; costs a launch).
 constexpr int64_t kDeferHaloPartials = 1 << 18;
+
+// Device address of the allocation-free apply's fixed scratch array on the current device
+// (noalloc.cu); the first call per device loads the array's module. pfem_mesh_create calls it.
+pfem_status noalloc_scratch(void** out);
 
 // Dynamic shared memory one tile CTA of launch_element_op needs.
 size_t element_op_smem(const DevPlan& P, int ops, pfem_dtype ct);

@@ -1,4 +1,4 @@
-// Serving: continuous batching of warm-started solves (Sec. 2.3.2: a platform receives
+// Serving: continuous batching of warm-started solves (Sec. "Warm-start": a platform receives
 // problems and refines the pretrained prediction by FE iterations).
 //
 // Requests arrive through pfem_serve_submit. Planner threads validate and tile their meshes
@@ -56,7 +56,7 @@ __global__ void init_state_kernel(PcgState* st, double tol, int max_iter, const 
   *st = s;
 }
 
-// keep the start's relative residual (the Sec. 2.3.2 skip-test quantity) for the report
+// keep the start's relative residual (the Sec. "Warm-start" skip-test quantity) for the report
 __global__ void save_init_rel_kernel(const PcgState* st, double* dst) { *dst = st->rel_true; }
 
 struct StateSlot {

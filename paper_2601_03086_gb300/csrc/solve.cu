@@ -1,4 +1,4 @@
-// Warm-started solvers on the device (Sec. 2.3.2 warm start; App. B linear system and
+// Warm-started solvers on the device (Sec. "Warm-start"; App. B linear system and
 // Newton-Raphson with load steps).
 //
 // Jacobi-PCG keeps every vector, dot and norm in FP64 on the GPU; the operator applications
@@ -56,6 +56,8 @@ struct SolverWS {
 };
 
 static int g_kernel_timing = 0;
+static long long g_barrier_spin_limit = kBarrierSpinLimit;  // persistent kernel's barrier waits
+static int g_absent_cta = -1;                               // failure-detection test hook
 
 __global__ void set_cond_kernel(cudaGraphConditionalHandle h, const PcgState* st) {
   cudaGraphSetConditional(h, (st->done == 0 && st->repl == 0) ? 1u : 0u);
@@ -287,7 +289,7 @@ static pfem_status pcg_run(pfem_mesh_t m, SolverWS* w, pfem_dtype ct, bool use_u
     }
     if (g_solver_mode == 0 && ct != PFEM_F64 && !w->persist_failed[ui]) {
       PersistArgs pa{use_u ? w->u : nullptr, w->x, w->r, w->dinv, {w->p, w->p2}, w->q, w->st, w->tile_part,
-                     w->ticket, m->red_partials, m->red_counter, w->bar, w->n};
+                     w->ticket, m->red_partials, m->red_counter, w->bar, w->n, g_barrier_spin_limit, g_absent_cta};
       st = launch_pcg_persistent(m->plan, ct, pa, s);
       if (st == PFEM_OK) continue;
       if (st != PFEM_ERR_UNSUPPORTED) return st;
@@ -384,6 +386,16 @@ pfem_status pfem_set_solver_mode(int32_t mode) {
     return PFEM_ERR_INVALID_ARG;
   }
   g_solver_mode = mode;
+  return PFEM_OK;
+}
+
+pfem_status pfem_set_barrier_test(int64_t spin_limit, int32_t absent_cta) {
+  if (absent_cta < -1) {
+    set_error("absent_cta must be -1 (none) or a CTA index");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  g_barrier_spin_limit = spin_limit > 0 ? (long long)spin_limit : kBarrierSpinLimit;
+  g_absent_cta = absent_cta;
   return PFEM_OK;
 }
 
@@ -550,7 +562,6 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
     result = PFEM_OK;  // again from the last converged state with half the increment
     PFEM_CUDA(cudaMemcpyAsync(w->u, w->uc, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
-  m->load_scale = saved_scale;
   if (st) return st;
   PFEM_CUDA(cudaMemcpyAsync(u_out, w->u, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, s));
   PFEM_CUDA(cudaStreamSynchronize(s));

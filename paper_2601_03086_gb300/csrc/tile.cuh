@@ -373,7 +373,7 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
   const CT* slot = reinterpret_cast<const CT*>(smem + L.slot);
   CT* part = static_cast<CT*>(P.partial) + (size_t)region * P.n_partials * 4;
   int32_t* count = P.halo_count + (size_t)region * P.n_partials;
-  const CT sc = A.out_scale ? CT(*A.out_scale) : CT(1);  // upstream factor (batched autograd)
+  const CT sc = A.out_scale ? CT(*static_cast<const VT*>(A.out_scale)) : CT(1);  // upstream factor (autograd)
   const bool defer = A.defer_halo != 0;
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     int slot_i = pbeg + l - ncomp;  // deferred: tile order, no load on the way

@@ -109,3 +109,44 @@ def test_unknown_ticket_and_drain():
     assert st == 0
     server.close()
     del PfemError
+
+
+def test_bench_size_requests_match_oracle_alone_and_mixed():
+    """Requests of the sizes the benchmark serves (~50k tets): a 20^3 cube (48,000 tets) zero
+    and warm started, and a 48x12x12 Neo-Hookean bar (41,472 tets, 10% stretch) warm started.
+    Served together they match the oracle (solutions within 1e-6, linear iteration counts
+    within the FP32 bar) and are bitwise the results each gives alone."""
+    P = pfem()
+    items = []
+    p = pi.cube_problem(20, seed=105)
+    m = fem.Mesh(p)
+    u_star, _, _ = solve.solve_linear(m, tol=1e-13)
+    for warm in (None, pi.make_warm_start(p, u_star, seed=11)):
+        items.append(dict(problem=p, u0=warm, solve="linear", steps=1, u_star=u_star))
+    pb = pi.bar_problem(48, 12, 12, seed=205, stretch=0.1)
+    mb = fem.Mesh(pb)
+    u5, _, _ = solve.solve_newton(mb, tol=1e-8, n_load_steps=5, direct=True)
+    ub_star, _, _ = solve.solve_newton(mb, u0=u5, tol=1e-12, n_load_steps=1, direct=True)
+    items.append(dict(problem=pb, u0=pi.make_warm_start(pb, ub_star, seed=13), solve="newton", steps=1,
+                      u_star=ub_star))
+    server = P.Server(16 << 30, max_slots=8)
+    mixed = _run(server, items, timeout=600.0)
+    server.close()
+    for r, (st, u, info) in zip(items, mixed):
+        assert st == 0, info
+        assert rel_l2(u, r["u_star"]) <= 1e-6
+        mm = fem.Mesh(r["problem"])
+        if r["solve"] == "linear":
+            _, it_ref, _ = solve.solve_linear(mm, u0=r["u0"], tol=1e-8)
+            assert abs(info["iterations"] - it_ref) <= max(2, int(0.015 * it_ref)), (info, it_ref)
+            assert info["rel_residual_true_f64"] < 1e-8
+        else:
+            _, n_ref, _ = solve.solve_newton(mm, u0=r["u0"], tol=1e-8, n_load_steps=1, direct=True)
+            assert abs(info["newton_iterations"] - n_ref) <= 2, (info, n_ref)
+            assert np.linalg.norm(fem.residual(mm, u)) <= 1.01e-8 * solve.newton_reference(mm, 1.0)
+    for r, (st, u, info) in zip(items, mixed):
+        alone = P.Server(16 << 30, max_slots=1)
+        st2, u2, info2 = _run(alone, [r], timeout=600.0)[0]
+        alone.close()
+        assert st2 == 0 and np.array_equal(u, u2), "result differs alone vs in the mix"
+        assert info["iterations"] == info2["iterations"]

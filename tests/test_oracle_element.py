@@ -110,13 +110,39 @@ def test_traction_resultant_3d():
     assert np.allclose(f.sum(axis=0), [0.0, 0.0, -0.1], atol=1e-14)
 
 
+def test_traction_per_node_3d_kuhn_face():
+    """Per-node consistent load on the z = 1 face of the Kuhn-split cube (App. B: each facet
+    node gets t |facet| / 3). The face is a square grid of spacing h with every square cut
+    along the same diagonal, so a node inside the face touches 6 triangles of area h^2 / 2
+    (share 6 (h^2/2) / 3 = h^2), a node on a face edge (not a corner) touches 3 (share
+    h^2 / 2); the 4 corners touch 1 or 2 (shares h^2 / 6 or h^2 / 3, two of each)."""
+    n = 5
+    h = 1.0 / n
+    t = -0.1
+    p = pi.cube_problem(n, seed=1)
+    m = fem.Mesh(p)
+    f = fem.external_force(m).reshape(-1, 3)
+    x = m.coords
+    top = np.isclose(x[:, 2], 1.0)
+    on_x = np.isclose(x[:, 0], 0.0) | np.isclose(x[:, 0], 1.0)
+    on_y = np.isclose(x[:, 1], 0.0) | np.isclose(x[:, 1], 1.0)
+    interior = top & ~on_x & ~on_y
+    edge = top & (on_x ^ on_y)
+    corner = top & on_x & on_y
+    assert interior.sum() == (n - 1) ** 2 and edge.sum() == 4 * (n - 1) and corner.sum() == 4
+    assert np.allclose(f[interior, 2], t * h * h, rtol=1e-13)
+    assert np.allclose(f[edge, 2], t * h * h / 2, rtol=1e-13)
+    assert np.allclose(np.sort(f[corner, 2] / (t * h * h)), [1 / 6, 1 / 6, 1 / 3, 1 / 3], rtol=1e-12)
+    assert np.allclose(f[~top], 0.0) and np.allclose(f[:, :2], 0.0)
+
+
 # --------------------------------------------------------------------------- patch test
 
 
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("kind", ["linear", "neohookean"])
 def test_patch_test_affine_field(dim, kind):
-    """Classical FE patch test (Sec. 5.2 cites it): affine u gives constant strain / F and
+    """Classical FE patch test (Sec. "Patch tests for PFEM" cites it): affine u gives constant strain / F and
     zero internal force at every node not on the patch boundary."""
     p = pi.small_problem(dim, kind, n=4, seed=11, permute=True)
     # the patch test needs one material over the patch (constant stress)
