@@ -28,8 +28,8 @@ timed on this host.
   and prints one JSON line with CUDA-event timings after warm-up.
 
 --impl reference times the FP64 CPU oracle (global sparse assembly + Jacobi-PCG) on the
-same workload: each step is a bounded sample of 100 PCG iterations of a warm solve,
-projected to the oracle's full iteration count (measured once in the warm-up).
+same workload: each step is one full warm-started solve of the cube (its own seeded warm
+start, as in the GPU arm) with the oracle's assembled K; assembly happens once, untimed.
 """
 
 import argparse
@@ -69,6 +69,31 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+# Algorithmic FP32 flops per 3-D simplex (FMA = 2 flops), counted from the element formulas
+# the kernels evaluate: geometry (edges, adjugate rows, det, 1/det) 43; gradient of a field
+# from corner values 54 (63 with the 1/det scale of the Neo-Hookean path); linear stress 18;
+# contraction T c_a with f_0 = -sum 51; linear energy 40; Neo-Hookean kinematic state (J - 1,
+# cof, H - I, ln J) 96; first Piola stress 55; its derivative along grad v 159; Psi 10.
+FLOPS_PER_ELEM = {
+    ("linear", "tangent"): 43 + 54 + 18 + 51,                       # 166
+    ("nh", "tangent"): 43 + 63 + 96 + 63 + 159 + 51,                # 475
+    ("linear", "energy+grad+hvp"): 43 + 54 + 40 + 18 + 51 + 54 + 18 + 51,   # 329
+    ("nh", "energy+grad+hvp"): 43 + 63 + 96 + 10 + 55 + 51 + 63 + 159 + 51,  # 591
+}
+
+
+def _fp32_peak_tflops():
+    """FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x the maximum SM clock
+    (MEASURED_PEAKS.json sm_max_mhz, else 2070 MHz)."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12, mhz
 
 
 class ClockSampler:
@@ -167,14 +192,18 @@ def cpu_oracle_warm_solve(n_sample=None):
     _, it_full, _ = solve.solve_linear(m, u0=warm, tol=TOL, K=K)
     t_full = time.perf_counter() - t0
     out = {"assembly_s": t_asm, "solve_s": t_full, "iterations": it_full}
-    if n_sample:
-        samples = []
-        for i in range(n_sample[0]):
+    if n_sample:  # (untimed warm-up solves, timed full solves), each with its own warm start
+        n_warm, n_timed = n_sample
+        solves, iters = [], []
+        for i in range(n_warm + n_timed):
             w = pi.make_warm_start(p, u_star, seed=21 + i)
             t0 = time.perf_counter()
-            solve.solve_linear(m, u0=w, tol=1e-30, max_iter=n_sample[1], K=K)
-            samples.append(time.perf_counter() - t0)
-        out["sample_s"] = samples
+            _, it, _ = solve.solve_linear(m, u0=w, tol=TOL, K=K)
+            if i >= n_warm:
+                solves.append(time.perf_counter() - t0)
+                iters.append(it)
+        out["solve_samples_s"] = solves
+        out["solve_samples_it"] = iters
     del np
     return out
 
@@ -194,20 +223,19 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return 0
     k, w = args.steps, args.warmup
-    # warm-up: one full warm solve (iteration count) + (w - 1) samples; timed: k samples
-    r = _run_oracle_child(["--oracle-worker", str(k + max(w - 1, 0)), "100"])
-    samples = r["sample_s"][max(w - 1, 0):]
-    per_it = sum(samples) / (len(samples) * 100.0)
-    solve_s = per_it * r["iterations"]
-    value = 1.0 / solve_s
+    # warm-up: one full warm solve in the setup plus (w - 1) more; timed: k full warm solves
+    r = _run_oracle_child(["--oracle-worker", str(max(w - 1, 0)), str(k)])
+    total = sum(r["solve_samples_s"])
+    solve_s = total / k
+    value = k / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": k,
         "warmup": w, "ms_per_step": solve_s * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": WORKLOAD,
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "per step 100 Jacobi-PCG iterations of a warm solve on the oracle's assembled "
-                                   "K (assembly %.1f s excluded), projected to its %d-iteration solve"
-                                   % (r["assembly_s"], r["iterations"])},
+                         "sample": "per step one full warm-started Jacobi-PCG solve to 1e-8 (%d-%d iterations) on "
+                                   "the oracle's assembled K (assembly %.1f s, once, untimed), single-threaded"
+                                   % (min(r["solve_samples_it"]), max(r["solve_samples_it"]), r["assembly_s"])},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "oracle_full_warm_solve_s": r["solve_s"],
     }
@@ -424,8 +452,8 @@ def main():
                                 "achieved_gbs": ach, "algorithmic_bytes": alg, "frac": ach / peak}
         if not args.quick:
             extras["roofline_large"] = _large_cube(P, pi, torch, peak, peak_kind)
-            extras["newton"] = _newton(P, pi, torch)
-            extras["batch_loss"] = _batch_loss(P, pi, torch, np)
+            extras["newton"] = _newton(P, pi, torch, peak)
+            extras["batch_loss"] = _batch_loss(P, pi, torch, np, peak)
             extras["serving"] = _serving(P, pi, torch, np)
 
     line = {
@@ -499,14 +527,22 @@ def _large_cube(P, pi, torch, peak, peak_kind):
     us = a.elapsed_time(b) * 1e3 / reps
     ach = alg / (us * 1e-6) / 1e9
     mesh.close()
+    fp32_peak, mhz = _fp32_peak_tflops()
+    tflops = FLOPS_PER_ELEM[("linear", "tangent")] * st["n_elems"] / (us * 1e-6) / 1e12
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": _committed_traffic("cube160_f32v"), "launch_us": us, "algorithmic_bytes": alg,
+            "elements_per_s": st["n_elems"] / (us * 1e-6),
+            "fp32": {"achieved_tflops": tflops, "peak_tflops": fp32_peak, "frac": tflops / fp32_peak,
+                     "flops_per_elem": FLOPS_PER_ELEM[("linear", "tangent")], "clock_mhz": mhz},
             "workload": "160^3 x 6 = 24,576,000 tets, 4,173,281 nodes, f32 vectors", "peak_kind": peak_kind}
 
 
-def _batch_loss(P, pi, torch, np):
+def _batch_loss(P, pi, torch, np, peak=None):
     """64-mesh ragged batch (cube / L-shape / holed plate, 5k-200k tets, mixed materials):
-    energy + gradient + Hessian-vector product of every mesh in one element launch."""
+    energy + gradient + Hessian-vector product of every mesh in one element launch. Also:
+    algorithmic bytes (per mesh 24 B/elem + per node X 12, mask 1, u, v, grad, hvp 12 each) and
+    flops (FLOPS_PER_ELEM) per evaluation against the HBM and FP32 peaks, and the FP32 results
+    against the same gradients and Hessian products evaluated per mesh in FP64."""
     items = pi.cfg4_batch()
     meshes = [P.Mesh(p) for p, _ in items]
     batch = P.Batch(meshes)
@@ -523,11 +559,34 @@ def _batch_loss(P, pi, torch, np):
     b.synchronize()
     ms = a.elapsed_time(b) / reps
     n_tets = int(sum(p["conn"].shape[0] for p, _ in items))
+    n_nodes = int(sum(p["coords"].shape[0] for p, _ in items))
+    alg = n_tets * 24 + n_nodes * (12 + 1 + 4 * 12)
+    flops = sum(p["conn"].shape[0] * FLOPS_PER_ELEM[("linear" if p["kind"] == "linear" else "nh",
+                                                      "energy+grad+hvp")] for p, _ in items)
+    _, g32, h32 = batch.eval(u, v, energy=False, grad=True, hvp=True)
+    g64, h64 = [], []
+    off = batch.offsets
+    for k, m in enumerate(meshes):
+        uk = u[off[k]:off[k + 1]].double().contiguous()
+        vk = v[off[k]:off[k + 1]].double().contiguous()
+        g64.append(P.pfem_energy_gradient(m, uk))
+        h64.append(P.pfem_energy_hvp(m, uk, vk))
+    g64, h64 = torch.cat(g64), torch.cat(h64)
+    err_g = float(torch.linalg.norm(g32.double() - g64) / torch.linalg.norm(g64))
+    err_h = float(torch.linalg.norm(h32.double() - h64) / torch.linalg.norm(h64))
     batch.close()
     for m in meshes:
         m.close()
+    fp32_peak, mhz = _fp32_peak_tflops()
+    tflops = flops / (ms * 1e-3) / 1e12
+    gbs = alg / (ms * 1e-3) / 1e9
     return {"meshes": len(items), "tets": n_tets, "ms_per_eval": ms, "evals_per_s": 1e3 / ms,
-            "tets_per_s": n_tets * 1e3 / ms, "ops": "energy + gradient + Hessian-vector, FP32 elements"}
+            "tets_per_s": n_tets * 1e3 / ms, "ops": "energy + gradient + Hessian-vector, FP32 elements",
+            "hbm": {"achieved_gbs": gbs, "peak_gbs": peak, "frac": gbs / peak if peak else None,
+                    "algorithmic_bytes": alg},
+            "fp32": {"achieved_tflops": tflops, "peak_tflops": fp32_peak, "frac": tflops / fp32_peak,
+                     "flops_per_eval": flops, "clock_mhz": mhz},
+            "fp32_vs_fp64_rel_l2": {"gradient": err_g, "hvp": err_h}}
 
 
 def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
@@ -544,8 +603,9 @@ def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
     to 1e-12 on this GPU plus the seeded smooth 1% perturbation (input preparation, untimed)."""
     reqs = pi.cfg5_requests(n_requests=n_req, seed=5, hi=hi)
     probs = [pi.request_problem(r) for r in reqs]
-    u0s = []
+    u0s, urefs = [], []
     for r, p in zip(reqs, probs):
+        urefs.append(None)
         if not r["warm"]:
             u0s.append(None)
             continue
@@ -561,7 +621,8 @@ def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
         if info["status"] != 0:  # no reference solution to perturb: served as a zero start
             u0s.append(None)
             continue
-        u0s.append(pi.make_warm_start(p, u.cpu().numpy(), seed=1 + r["seed"] % 100000))
+        urefs[-1] = u.cpu().numpy()  # FP64-operator solution to 1e-12
+        u0s.append(pi.make_warm_start(p, urefs[-1], seed=1 + r["seed"] % 100000))
 
     def steps(r, u0):
         return 1 if (r["kind"] == "linear" or u0 is not None) else 5
@@ -580,17 +641,20 @@ def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
     for mode_name, mode in (("plain_loop", MODES["plain"]), ("graph_loop", MODES["graph"])):
         P.pfem_set_solver_mode(mode)
         torch.cuda.synchronize()
-        lat, ok = [], 0
+        lat, ok, plan_s = [], 0, 0.0
         t0 = time.perf_counter()
         for r, p, u0 in zip(reqs, probs, u0s):
             a = time.perf_counter()
-            m = P.Mesh(p)
+            m = P.Mesh(p)  # host planning + upload (the server does this on planner threads)
+            b = time.perf_counter()
             _, info = solve_one(m, r, u0)
             m.close()
             lat.append(time.perf_counter() - a)
+            plan_s += b - a
             ok += info["status"] == 0
         wall = time.perf_counter() - t0
         out[mode_name] = {"solves_per_s": n_req / wall, "wall_s": wall, "converged": ok,
+                          "plan_upload_s": plan_s, "solves_per_s_excluding_planning": n_req / (wall - plan_s),
                           "solve_ms_p50": 1e3 * _pct(lat, 0.5), "solve_ms_p99": 1e3 * _pct(lat, 0.99)}
     P.pfem_set_solver_mode(MODES["graph"])
 
@@ -613,7 +677,7 @@ def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
             if k not in done:
                 res = server.poll(t)
                 if res is not None:
-                    done[k] = (time.perf_counter() - t0, res[0], res[2])
+                    done[k] = (time.perf_counter() - t0, res[0], res[2], res[1])
         if time.perf_counter() - t0 > 900.0:
             raise RuntimeError("served requests did not finish in 900 s")
         time.sleep(0.0005)
@@ -624,12 +688,24 @@ def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
                      "converged": sum(done[k][1] == 0 for k in range(n_req)),
                      "latency_ms_p50": 1e3 * _pct(lat, 0.5), "latency_ms_p99": 1e3 * _pct(lat, 0.99),
                      "pcg_iterations_total": int(sum(done[k][2]["iterations"] for k in range(n_req)))}
+    errs = [float(np.linalg.norm(done[k][3] - urefs[k]) / np.linalg.norm(urefs[k]))
+            for k in range(n_req) if urefs[k] is not None and done[k][1] == 0]
+    out["served"]["fp32_vs_fp64_rel_l2"] = {"requests": len(errs), "max": max(errs) if errs else None,
+                                            "median": _pct(errs, 0.5) if errs else None,
+                                            "reference": "FP64-operator solve to 1e-12 of each warm request"}
     out["speedup_vs_plain_loop"] = out["served"]["solves_per_s"] / out["plain_loop"]["solves_per_s"]
+    out["speedup_vs_plain_loop_excluding_planning"] = (out["served"]["solves_per_s"] /
+                                                       out["plain_loop"]["solves_per_s_excluding_planning"])
     out["speedup_vs_graph_loop"] = out["served"]["solves_per_s"] / out["graph_loop"]["solves_per_s"]
     return out
 
 
-def _newton(P, pi, torch):
+def _newton(P, pi, torch, peak=None):
+    """Neo-Hookean bar (config 3): zero start with 5 load steps, warm start with 1; the warm
+    solve again in FP64 element arithmetic (FP32-vs-FP64 solution difference) and once in the
+    plain loop with kernel timing (the inner PCG-fused Neo-Hookean apply against the HBM and
+    FP32 peaks: algorithmic bytes 24 B/elem + per node X 12, mask 1, u 24 and five FP64
+    vectors 120; flops FLOPS_PER_ELEM[nh, tangent])."""
     p = pi.cfg3_bar()
     mesh = P.Mesh(p)
     out = {}
@@ -645,6 +721,27 @@ def _newton(P, pi, torch):
     uw, iw = P.pfem_solve_newton(mesh, wd, tol=1e-8, n_load_steps=1, inner_tol=1e-8)
     torch.cuda.synchronize()
     out["warm_1step"] = {"s": time.perf_counter() - t0, "newton": iw["newton_iterations"], "pcg": iw["iterations"]}
+    u64, i64 = P.pfem_solve_newton(mesh, wd, tol=1e-8, n_load_steps=1, inner_tol=1e-8, precision="f64")
+    out["fp32_vs_fp64_rel_l2"] = float(torch.linalg.norm(uw - u64) / torch.linalg.norm(u64))
+    out["fp64_newton"] = i64["newton_iterations"]
+    st = mesh.stats()
+    mode = MODES["plain"]
+    P.pfem_set_solver_mode(mode)
+    P.pfem_set_kernel_timing(1)
+    _, ti = P.pfem_solve_newton(mesh, wd, tol=1e-8, n_load_steps=1, inner_tol=1e-8)
+    P.pfem_set_kernel_timing(0)
+    P.pfem_set_solver_mode(MODES["graph"])
+    nt = max(ti["timed_iterations"], 1)
+    us = 1e3 * ti["apply_ms"] / nt
+    alg = st["n_elems"] * 24 + st["n_nodes"] * (12 + 1 + 24 + 5 * 24)
+    fp32_peak, mhz = _fp32_peak_tflops()
+    tflops = FLOPS_PER_ELEM[("nh", "tangent")] * st["n_elems"] / (us * 1e-6) / 1e12
+    out["inner_apply"] = {"kernel": "tile_kernel<3,neohookean,tangent+PCG,f64 vectors,f32>", "launch_us": us,
+                          "launches_timed": ti["timed_iterations"], "algorithmic_bytes": alg,
+                          "hbm_frac": alg / (us * 1e-6) / 1e9 / peak if peak else None,
+                          "fp32_tflops": tflops, "fp32_frac": tflops / fp32_peak, "clock_mhz": mhz,
+                          "update_kernel_us": 1e3 * ti["update_ms"] / nt,
+                          "note": "98k-tet working set is L2-resident; events around each fused apply"}
     out["workload"] = "NH bar 64x16x16 hexes x 6 = 98,304 tets, 20% stretch, tol 1e-8, inner PCG 1e-8"
     mesh.close()
     return out

@@ -92,6 +92,7 @@ size_t mesh_arena_bytes(const HostPlan& hp) {
   take(hp.halo_rec.size() * 4);
   take(hp.halo_node.size() * 4);
   take(hp.halo_seq.size() * 4);
+  take((size_t)hp.n_nodes * 8);
   take((size_t)std::max<int64_t>(hp.n_partials, 1) * kMaxRegions * sizeof(int32_t));
   take((size_t)std::max<int64_t>(hp.n_partials, 1) * 4 * sizeof(double) * kMaxRegions);
   take((size_t)std::max<int64_t>(hp.n_tiles(), 1) * sizeof(double));
@@ -112,6 +113,13 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   void* cuda_stream = stream;
   const int dim = hp.dim;
   const int64_t nd = hp.n_nodes * dim;
+  // per node {first, count} of its contiguous halo partials (count 0 for complete nodes)
+  std::vector<int32_t> node_part((size_t)hp.n_nodes * 2, 0);
+  for (int64_t h = 0; h < hp.n_halo(); ++h) {
+    const int64_t gid = (int64_t)((uint32_t)hp.halo_info[(size_t)h] & kInfoIdMask);
+    node_part[(size_t)gid * 2] = hp.halo_ptr[(size_t)h];
+    node_part[(size_t)gid * 2 + 1] = hp.halo_ptr[(size_t)h + 1] - hp.halo_ptr[(size_t)h];
+  }
   std::vector<float> fext_f(fext.size());
   for (size_t i = 0; i < fext.size(); ++i) fext_f[i] = (float)fext[i];
   std::vector<double> vals((size_t)nd, 0.0);
@@ -140,6 +148,7 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   const size_t o_hr = ab.take(hp.halo_rec.size() * 4);
   const size_t o_hn = ab.take(hp.halo_node.size() * 4);
   const size_t o_hq = ab.take(hp.halo_seq.size() * 4);
+  const size_t o_np = ab.take((size_t)hp.n_nodes * 8);
   const size_t o_hc = ab.take((size_t)std::max<int64_t>(hp.n_partials, 1) * kMaxRegions * sizeof(int32_t));
   const size_t o_pa = ab.take((size_t)std::max<int64_t>(hp.n_partials, 1) * 4 * sizeof(double) * kMaxRegions);
   const size_t o_te = ab.take((size_t)std::max<int64_t>(nt, 1) * sizeof(double));
@@ -197,7 +206,7 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
       (st = upload(base, o_fh, hp.fan_head, s)) || (st = upload(base, o_sc, hp.step_code, s)) ||
       (st = upload(base, o_mf, hp.step_mat_f, s)) || (st = upload(base, o_md, hp.step_mat_d, s)) ||
       (st = upload(base, o_hr, hp.halo_rec, s)) || (st = upload(base, o_hn, hp.halo_node, s)) ||
-      (st = upload(base, o_hq, hp.halo_seq, s)) ||
+      (st = upload(base, o_hq, hp.halo_seq, s)) || (st = upload(base, o_np, node_part, s)) ||
       (st = upload(base, o_fe, fext, s)) ||
       (st = upload(base, o_ff, fext_f, s)) || (st = upload(base, o_dv, vals, s)) || (st = upload(base, o_dm, mask, s)))
     return fail(st);
@@ -231,6 +240,7 @@ pfem_status mesh_upload(const HostPlan& hp, const std::vector<double>& fext, con
   P.halo_rec = reinterpret_cast<const int4*>(base + o_hr);
   P.halo_node = reinterpret_cast<const int4*>(base + o_hn);
   P.halo_seq = reinterpret_cast<const int32_t*>(base + o_hq);
+  P.node_part = reinterpret_cast<const int2*>(base + o_np);
   P.halo_count = reinterpret_cast<int32_t*>(base + o_hc);
   P.partial = base + o_pa;
   P.tile_energy = reinterpret_cast<double*>(base + o_te);

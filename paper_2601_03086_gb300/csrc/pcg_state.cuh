@@ -12,27 +12,47 @@ namespace pfem {
 // (FP64 replacement / convergence check by the host, iteration cap, or the next beta).
 // The state is read through L2 only: inside a persistent launch another CTA may have
 // written it since this one last looked.
+// The decision itself, on values (so that a kernel can take it from local copies of the
+// state): the new iteration count and relative residual, then a non-finite stop, a request
+// for an FP64 replacement, the iteration cap, or the next beta and rho (next = 1).
+struct PcgStep {
+  int iter, done, repl, next;
+  double rel, beta, rho;
+};
+__device__ __forceinline__ PcgStep pcg_decide(int iter0, int done, int max_iter, double ref, double tol, double thr,
+                                              double rho, double rz, double rr) {
+  PcgStep s{iter0 + 1, done, 0, 0, sqrt(rr) / ref, 0.0, rho};
+  if (!isfinite(rz) || !isfinite(rr)) {
+    if (done == 0) s.done = PCG_NONFINITE;
+  } else if (done == 0) {
+    if (s.rel < tol || s.rel < thr) {
+      s.repl = 1;  // the host verifies / replaces with the FP64 true residual
+    } else if (s.iter >= max_iter) {
+      s.done = PCG_MAXITER;
+    } else {
+      s.next = 1;
+      s.beta = rz / rho;
+      s.rho = rz;
+    }
+  }
+  return s;
+}
+
 __device__ __forceinline__ void pcg_finish_update(PcgState* st, double rz, double rr) {
   // every field this needs, loaded before the first store (one round trip)
-  const int iter = __ldcg(&st->iter) + 1;
+  const int iter = __ldcg(&st->iter);
   const int done = __ldcg(&st->done);
   const int max_iter = __ldcg(&st->max_iter);
   const double ref = __ldcg(&st->ref), tol = __ldcg(&st->tol), thr = __ldcg(&st->repl_threshold);
   const double rho = __ldcg(&st->rho);
-  st->iter = iter;
-  const double rel = sqrt(rr) / ref;
-  st->rel = rel;
-  if (!isfinite(rz) || !isfinite(rr)) {
-    if (done == 0) st->done = PCG_NONFINITE;
-  } else if (done == 0) {
-    if (rel < tol || rel < thr) {
-      st->repl = 1;  // the host verifies / replaces with the FP64 true residual
-    } else if (iter >= max_iter) {
-      st->done = PCG_MAXITER;
-    } else {
-      st->beta = rz / rho;
-      st->rho = rz;
-    }
+  const PcgStep s = pcg_decide(iter, done, max_iter, ref, tol, thr, rho, rz, rr);
+  st->iter = s.iter;
+  st->rel = s.rel;
+  if (s.done != done) st->done = s.done;
+  if (s.repl) st->repl = 1;
+  if (s.next) {
+    st->beta = s.beta;
+    st->rho = s.rho;
   }
 }
 

@@ -149,6 +149,8 @@ struct DevPlan {
   const int4* halo_rec;  // per (tile, halo node) pair in tile order
   const int4* halo_node; // per halo node {first CSR position, count, info, 0}
   const int32_t* halo_seq;  // per CSR position: tile-order index of its partial (deferred mode)
+  const int2* node_part;    // per node: {first, count} of its contiguous halo partials (count 0:
+                            // complete node, written by the tile holding all its elements)
   int32_t* halo_count;   // per region x partial slot (used at each halo node's first slot):
                          // partials published so far (reset by the last)
   void* partial;         // scratch: per region n_partials slots of 4 compute-type values
@@ -220,12 +222,18 @@ struct PcgArgs {
   int alpha_by_update;    // 1: tiles only store their sums; the update kernel forms alpha
 };
 
-// Grid barrier of the persistent PCG kernel (zeroed before every launch).
+// Grid barrier of the persistent PCG kernels (zeroed before every launch). The arrival
+// counter and the words the waiting CTAs poll sit on different 128-byte lines, so that the
+// polls do not slow the arrivals.
 struct GridBar {
   unsigned int count;  // arrivals at the current barrier
+  unsigned int pad0[31];
   unsigned int gen;    // completed barriers
   int err;             // 1 = some CTA gave up waiting
-  int pad;
+  // scalars the last CTA to arrive computes and publishes with the release (same line as gen)
+  int b_stop, b_iter;
+  double b_alpha, b_beta, b_rho;
+  unsigned int pad1[20];
 };
 
 // Buffers of the persistent PCG kernel: one launch runs whole iterations (fused direction /

@@ -168,6 +168,11 @@ struct pfem_server_s {
   size_t cap_reqs = 0, cap_btile = 0, cap_ublk = 0;
   int n_apply = 0, n_update = 0, max_local = 1, slot_cap = 4, step_cap = 1;
   std::vector<int> active_index;   // position of each active request in the tables
+  // one chunk (kChunk shared steps, the state gather and its read-back) captured as a CUDA
+  // graph for the current tables; captured again whenever the tables change
+  cudaGraphExec_t chunk_exec = nullptr;
+  int64_t chunk_kernels = 0;       // kernels per replay of the chunk graph
+  bool graph_failed = false;       // capture unavailable: plain launches
 };
 
 namespace pfem {
@@ -594,9 +599,58 @@ void plan_worker(pfem_server_s* S) {
   }
 }
 
+constexpr int kChunk = 8;  // shared steps between two read-backs of the solves' scalars
+
+// The work of one chunk, enqueued on s: kChunk shared steps, then every active solve's state
+// gathered into one table and copied to the pinned host mirror.
+pfem_status enqueue_chunk(pfem_server_s* S, cudaStream_t s) {
+  pfem_status st;
+  for (int k = 0; k < kChunk; ++k)
+    if ((st = launch_serve_step(S->d_reqs, S->d_btile, S->n_apply, S->d_ublk, S->n_update, S->max_local,
+                                S->slot_cap, S->step_cap, s)))
+      return st;
+  const int na = (int)S->active.size();
+  gather_states_kernel<<<(na + 127) / 128, 128, 0, s>>>(S->d_stp, S->d_auxp, S->d_invp, na, S->d_slots);
+  PFEM_COUNT_LAUNCH();
+  PFEM_CUDA(cudaGetLastError());
+  PFEM_CUDA(cudaMemcpyAsync(S->h_slots, S->d_slots, (size_t)na * sizeof(StateSlot), cudaMemcpyDeviceToHost, s));
+  return PFEM_OK;
+}
+
+// Captures the chunk for the current tables into S->chunk_exec (replacing the old graph).
+pfem_status capture_chunk(pfem_server_s* S) {
+  if (S->chunk_exec) {
+    cudaGraphExecDestroy(S->chunk_exec);
+    S->chunk_exec = nullptr;
+  }
+  // a step with no blocks launches nothing but sets the apply kernel's shared-memory limit,
+  // which is a function attribute and stays outside the capture
+  pfem_status pre = launch_serve_step(S->d_reqs, S->d_btile, 0, S->d_ublk, 0, S->max_local, S->slot_cap,
+                                      S->step_cap, S->stream);
+  if (pre != PFEM_OK) return pre;
+  const int64_t before = g_kernel_launches;
+  PFEM_CUDA(cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal));
+  const pfem_status st = enqueue_chunk(S, S->stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(S->stream, &g);
+  S->chunk_kernels = g_kernel_launches - before;
+  g_kernel_launches = before;  // captured, not run: each replay is counted when launched
+  if (st != PFEM_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st != PFEM_OK ? st : cuda_fail(e, "capturing the serving chunk");
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&S->chunk_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) {
+    S->chunk_exec = nullptr;
+    return cuda_fail(ei, "instantiating the serving chunk");
+  }
+  return PFEM_OK;
+}
+
 void worker_loop(pfem_server_s* S) {
   cudaSetDevice(S->device);
-  const int chunk = 8;
   for (;;) {
     // ---- admission (FIFO: a request waits for the one ahead of it)
     std::vector<Request*> admitted, rejected;
@@ -643,20 +697,23 @@ void worker_loop(pfem_server_s* S) {
       S->dirty = true;
     }
     if (S->active.empty()) continue;
-    if (S->dirty && rebuild_tables(S) != PFEM_OK) {
-      for (Request* R : S->active) finish(S, R, PFEM_ERR_CUDA);
-      S->active.clear();
-      S->dirty = true;
-      continue;
+    if (S->dirty) {
+      if (rebuild_tables(S) != PFEM_OK) {
+        for (Request* R : S->active) finish(S, R, PFEM_ERR_CUDA);
+        S->active.clear();
+        S->dirty = true;
+        continue;
+      }
+      if (!S->graph_failed && capture_chunk(S) != PFEM_OK) S->graph_failed = true;  // plain launches from now on
     }
     // ---- a chunk of shared steps, then one read-back of every solve's scalars
-    for (int k = 0; k < chunk; ++k)
-      launch_serve_step(S->d_reqs, S->d_btile, S->n_apply, S->d_ublk, S->n_update, S->max_local, S->slot_cap, S->step_cap,
-                        S->stream);
     const int na = (int)S->active.size();
-    gather_states_kernel<<<(na + 127) / 128, 128, 0, S->stream>>>(S->d_stp, S->d_auxp, S->d_invp, na, S->d_slots);
-    PFEM_COUNT_LAUNCH();
-    cudaMemcpyAsync(S->h_slots, S->d_slots, (size_t)na * sizeof(StateSlot), cudaMemcpyDeviceToHost, S->stream);
+    bool launched = false;
+    if (S->chunk_exec && !S->graph_failed) {
+      launched = cudaGraphLaunch(S->chunk_exec, S->stream) == cudaSuccess;
+      if (launched) g_kernel_launches += S->chunk_kernels;
+    }
+    if (!launched) enqueue_chunk(S, S->stream);
     if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
       for (Request* R : S->active) finish(S, R, PFEM_ERR_CUDA);
       S->active.clear();
@@ -847,6 +904,7 @@ void pfem_serve_destroy(pfem_server_t S) {
     delete R;
   }
   cudaStreamSynchronize(S->stream);  // pooled memory returned before the pool goes
+  if (S->chunk_exec) cudaGraphExecDestroy(S->chunk_exec);
   cudaFree(S->d_reqs);
   cudaFree(S->d_btile);
   cudaFree(S->d_ublk);

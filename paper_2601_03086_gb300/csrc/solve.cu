@@ -96,7 +96,7 @@ static pfem_status ws_get(pfem_mesh_t m, SolverWS** out) {
   w->n = m->n_dofs;
   const size_t vb = ((size_t)w->n * sizeof(double) + 255) & ~size_t(255);
   const size_t tb = ((size_t)std::max(m->plan.n_tiles, 1) * sizeof(double) + 255) & ~size_t(255);
-  w->bytes = 11 * vb + tb + 768;
+  w->bytes = 11 * vb + tb + 1024;
   cudaError_t e = cudaMalloc(&w->block, w->bytes);
   if (e != cudaSuccess) {
     delete w;

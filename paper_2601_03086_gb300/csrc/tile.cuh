@@ -136,9 +136,8 @@ __device__ __forceinline__ void final_write(const DevPlan& P, const OpArgs& A, i
 
 // One fan pass for output OUT (or energy only when OUT < 0): thread f walks the ring of fan
 // f once (see pfem_internal.h), evaluates its simplices in ring order and writes one slot per
-// (fan, node). PAP: accumulate v . (A v) restricted to the fan's nodes into e_acc (tangent
-// pass of the PCG-fused apply; summed over fans this is v . A v).
-template <int DIM, int KIND, int OUT, bool ENERGY, bool COUNT, typename CT, bool PAP = false>
+// (fan, node).
+template <int DIM, int KIND, int OUT, bool ENERGY, bool COUNT, typename CT>
 __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<CT>& L, int nf, double& e_acc,
                                          int& n_inv) {
   constexpr int NV = DIM + 1;
@@ -159,12 +158,6 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
     const int sl = soff[code & 1023u] + (int)(code >> 10);
     st4(slot + 4 * sl, acc[0], acc[1], DIM == 3 ? acc[DIM - 1] : CT(0), CT(0));
   };
-  auto dot3 = [](const CT (&a)[3], const CT (&b)[DIM]) {
-    CT t = a[0] * b[0];
-#pragma unroll
-    for (int i = 1; i < DIM; ++i) t = fma(a[i], b[i], t);
-    return t;
-  };
   for (int f = threadIdx.x; f < nf; f += blockDim.x) {
     const ushort4 hd = shead[f];
     const int k = hd.w;
@@ -173,7 +166,6 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
     if constexpr (NEED_GU) ld4(su + 4 * (hd.x & 1023), u0);
     if constexpr (NEED_GV) ld4(sv + 4 * (hd.x & 1023), v0);
     CT H[3] = {CT(0), CT(0), CT(0)}, duH[3] = {CT(0), CT(0), CT(0)}, dvH[3] = {CT(0), CT(0), CT(0)};
-    CT v1[3] = {CT(0), CT(0), CT(0)};
     if constexpr (DIM == 3) {
       CT t[4];
       ld4(sx + 4 * (hd.y & 1023), t);
@@ -187,10 +179,7 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
       if constexpr (NEED_GV) {
         ld4(sv + 4 * (hd.y & 1023), t);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          dvH[i] = t[i] - v0[i];
-          v1[i] = t[i];
-        }
+        for (int i = 0; i < 3; ++i) dvH[i] = t[i] - v0[i];
       }
     }
     // ring node records (x, u, v) fetched one step ahead of their use
@@ -203,8 +192,8 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
       if constexpr (NEED_GU) ld4(su + 4 * l, g.u);
       if constexpr (NEED_GV) ld4(sv + 4 * l, g.v);
     };
-    // ring node state: edge from h_0, H x edge, field differences from h_0, raw v (PAP)
-    auto derive_ring = [&](const Ring& g, CT (&E)[3], CT (&Q)[3], CT (&du)[3], CT (&dv)[3], CT (&vr)[3]) {
+    // ring node state: edge from h_0, H x edge, field differences from h_0
+    auto derive_ring = [&](const Ring& g, CT (&E)[3], CT (&Q)[3], CT (&du)[3], CT (&dv)[3]) {
 #pragma unroll
       for (int i = 0; i < 3; ++i) E[i] = g.x[i] - x0[i];
       if constexpr (DIM == 3) {
@@ -218,21 +207,17 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
       }
       if constexpr (NEED_GV) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          dv[i] = g.v[i] - v0[i];
-          vr[i] = g.v[i];
-        }
+        for (int i = 0; i < 3; ++i) dv[i] = g.v[i] - v0[i];
       }
     };
     CT acc0[DIM], acc1[DIM], accc[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) acc0[i] = acc1[i] = accc[i] = CT(0);
     unsigned cc = hd.z;
-    CT Ec[3], Qc[3] = {CT(0), CT(0), CT(0)}, duc[3] = {CT(0), CT(0), CT(0)}, dvc[3] = {CT(0), CT(0), CT(0)},
-              vc[3] = {CT(0), CT(0), CT(0)};
+    CT Ec[3], Qc[3] = {CT(0), CT(0), CT(0)}, duc[3] = {CT(0), CT(0), CT(0)}, dvc[3] = {CT(0), CT(0), CT(0)};
     Ring gnext;
     fetch_ring(cc, gnext);
-    derive_ring(gnext, Ec, Qc, duc, dvc, vc);
+    derive_ring(gnext, Ec, Qc, duc, dvc);
     int s = f;  // step record of the tile (step-major: step i of fan f at sum_{j<i} cnt_j + f)
     unsigned cnext = 0;
     M2 mnext{};
@@ -241,13 +226,11 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
       mnext = smat[s];
       fetch_ring(cnext, gnext);
     }
-    CT e_fan = CT(0);  // PAP: this fan's share of v . A v
     for (int i = 0; i < k; ++i) {
       const unsigned cn = cnext;
       const CT mu = mnext.x, lam = mnext.y;
-      CT En[3], Qn[3] = {CT(0), CT(0), CT(0)}, dun[3] = {CT(0), CT(0), CT(0)}, dvn[3] = {CT(0), CT(0), CT(0)},
-                vn[3] = {CT(0), CT(0), CT(0)};
-      derive_ring(gnext, En, Qn, dun, dvn, vn);
+      CT En[3], Qn[3] = {CT(0), CT(0), CT(0)}, dun[3] = {CT(0), CT(0), CT(0)}, dvn[3] = {CT(0), CT(0), CT(0)};
+      derive_ring(gnext, En, Qn, dun, dvn);
       s += scnt[i];
       if (i + 1 < k) {  // the next step's record and ring node, in flight during this simplex
         cnext = scode[s];
@@ -336,7 +319,6 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
           accc[j] += out[HS][j];
         }
         put(cc, accc);  // ring node i is complete: it touches simplices i - 1 and i only
-        if constexpr (PAP) e_fan += dot3(vc, accc);
 #pragma unroll
         for (int j = 0; j < DIM; ++j) accc[j] = out[HS + 1][j];
       }
@@ -347,27 +329,32 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
         Qc[j] = Qn[j];
         duc[j] = dun[j];
         dvc[j] = dvn[j];
-        vc[j] = vn[j];
       }
     }
     if constexpr (OUT >= 0) {
       put(cc, accc);
       put(hd.x, acc0);
       if constexpr (DIM == 3) put(hd.y, acc1);
-      if constexpr (PAP) {
-        CT v0c[3] = {v0[0], v0[1], v0[2]};
-        e_fan += dot3(vc, accc) + dot3(v0c, acc0);
-        if constexpr (DIM == 3) e_fan += dot3(v1, acc1);
-        e_acc += (double)e_fan;
-      }
     }
   }
+}
+
+// p_l . (A_tile p)_l of one tile node in the element precision (summed in FP64 over the tile's
+// nodes this is the tile's share of p . A p: every element contribution to node l sits in
+// one of l's slots)
+template <int DIM, typename CT>
+__device__ __forceinline__ double pap_node(const CT* v, const CT (&acc)[4]) {
+  CT d = v[0] * acc[0];
+#pragma unroll
+  for (int i = 1; i < DIM; ++i) d = fma(v[i], acc[i], d);
+  return (double)d;
 }
 
 template <int DIM, int OUT, typename VT, typename CT, bool PCG = false>
 __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, unsigned char* smem,
                                           const SmemLayout<CT>& L, int nl, int ncomp, int pbeg, int region,
-                                          const double* p_old = nullptr, double* p_new = nullptr, double beta = 0.0) {
+                                          const double* p_old = nullptr, double* p_new = nullptr, double beta = 0.0,
+                                          double* e_pap = nullptr) {
   const int* soff = reinterpret_cast<const int*>(smem + L.off);
   const int* sinfo = reinterpret_cast<const int*>(smem + L.info);
   const CT* slot = reinterpret_cast<const CT*>(smem + L.slot);
@@ -386,6 +373,7 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
 #pragma unroll
       for (int i = 0; i < DIM; ++i) acc[i] += t[i];
     }
+    if constexpr (PCG) *e_pap += pap_node<DIM, CT>(reinterpret_cast<const CT*>(smem + L.v) + 4 * l, acc);
     if (l < ncomp) {
       const unsigned info = (unsigned)sinfo[l];
       final_write<DIM, OUT, VT, CT, PCG>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, acc, sc);
@@ -588,9 +576,9 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
     fan_pass<DIM, KIND, -1, true, true, CT>(smem, L, nf, e_acc, n_inv);
   }
   if constexpr ((OPS & OP_TANGENT) != 0) {
-    fan_pass<DIM, KIND, OUT_TAN, false, (OPS & (OP_RESIDUAL | OP_ENERGY)) == 0, CT, PCG>(smem, L, nf, e_acc, n_inv);
+    fan_pass<DIM, KIND, OUT_TAN, false, (OPS & (OP_RESIDUAL | OP_ENERGY)) == 0, CT>(smem, L, nf, e_acc, n_inv);
     __syncthreads();
-    node_pass<DIM, OUT_TAN, VT, CT, PCG>(P, A, smem, L, nl, ncomp, pbeg, region++, p_old, p_new, beta);
+    node_pass<DIM, OUT_TAN, VT, CT, PCG>(P, A, smem, L, nl, ncomp, pbeg, region++, p_old, p_new, beta, &e_acc);
     __syncthreads();
   }
   if constexpr ((OPS & OP_DIAG) != 0) {

@@ -125,8 +125,8 @@ def test_bench_size_requests_match_oracle_alone_and_mixed():
         items.append(dict(problem=p, u0=warm, solve="linear", steps=1, u_star=u_star))
     pb = pi.bar_problem(48, 12, 12, seed=205, stretch=0.1)
     mb = fem.Mesh(pb)
-    u5, _, _ = solve.solve_newton(mb, tol=1e-8, n_load_steps=5, direct=True)
-    ub_star, _, _ = solve.solve_newton(mb, u0=u5, tol=1e-12, n_load_steps=1, direct=True)
+    u5, _, _ = solve.solve_newton(mb, tol=1e-8, n_load_steps=5)
+    ub_star, _, _ = solve.solve_newton(mb, u0=u5, tol=1e-12, n_load_steps=1, inner_tol=1e-12)
     items.append(dict(problem=pb, u0=pi.make_warm_start(pb, ub_star, seed=13), solve="newton", steps=1,
                       u_star=ub_star))
     server = P.Server(16 << 30, max_slots=8)
@@ -141,7 +141,7 @@ def test_bench_size_requests_match_oracle_alone_and_mixed():
             assert abs(info["iterations"] - it_ref) <= max(2, int(0.015 * it_ref)), (info, it_ref)
             assert info["rel_residual_true_f64"] < 1e-8
         else:
-            _, n_ref, _ = solve.solve_newton(mm, u0=r["u0"], tol=1e-8, n_load_steps=1, direct=True)
+            _, n_ref, _ = solve.solve_newton(mm, u0=r["u0"], tol=1e-8, n_load_steps=1)
             assert abs(info["newton_iterations"] - n_ref) <= 2, (info, n_ref)
             assert np.linalg.norm(fem.residual(mm, u)) <= 1.01e-8 * solve.newton_reference(mm, 1.0)
     for r, (st, u, info) in zip(items, mixed):
