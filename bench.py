@@ -262,6 +262,7 @@ def main():
     ap.add_argument("--kind", choices=["linear", "nh"], default="linear", help="probe apply: material")
     ap.add_argument("--op", choices=["tangent", "residual"], default="tangent", help="probe apply: operator")
     ap.add_argument("--max-iter", type=int, default=100000, help="probe solve: PCG iteration cap")
+    ap.add_argument("--k", type=int, default=0, help="probe apply: k > 0 applies to k vectors at once")
     args = ap.parse_args()
     if args.oracle_worker is not None:
         print(json.dumps(cpu_oracle_warm_solve(tuple(args.oracle_worker))))
@@ -526,12 +527,34 @@ def _large_cube(P, pi, torch, peak, peak_kind):
     b.synchronize()
     us = a.elapsed_time(b) * 1e3 / reps
     ach = alg / (us * 1e-6) / 1e9
+    # several right-hand sides per pass over the element data (pfem_tangent_apply_multi):
+    # algorithmic bytes per launch = 24 B/elem + (X 12 + mask 1) B/node once + (v 12 + y 12)
+    # B/node per vector
+    multi = []
+    for k in (1, 2, 4, 6):
+        V = torch.randn((k, mesh.n_dofs), dtype=torch.float32, device="cuda")
+        Y = torch.empty_like(V)
+        for _ in range(2):
+            P.pfem_tangent_apply_multi(mesh, V, Y)
+        reps_k = 10
+        a, b = _events(torch)
+        a.record()
+        for _ in range(reps_k):
+            P.pfem_tangent_apply_multi(mesh, V, Y)
+        b.record()
+        b.synchronize()
+        us_k = a.elapsed_time(b) * 1e3 / reps_k
+        alg_k = st["n_elems"] * 24 + st["n_nodes"] * (13 + 24 * k)
+        multi.append({"k": k, "launch_us": us_k, "us_per_rhs": us_k / k, "algorithmic_bytes": alg_k,
+                      "bytes_per_rhs": alg_k / k, "achieved_gbs": alg_k / (us_k * 1e-6) / 1e9,
+                      "frac": alg_k / (us_k * 1e-6) / 1e9 / peak, "rhs_applies_per_s": k / (us_k * 1e-6)})
+        del V, Y
     mesh.close()
     fp32_peak, mhz = _fp32_peak_tflops()
     tflops = FLOPS_PER_ELEM[("linear", "tangent")] * st["n_elems"] / (us * 1e-6) / 1e12
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": _committed_traffic("cube160_f32v"), "launch_us": us, "algorithmic_bytes": alg,
-            "elements_per_s": st["n_elems"] / (us * 1e-6),
+            "elements_per_s": st["n_elems"] / (us * 1e-6), "multi_rhs": multi,
             "fp32": {"achieved_tflops": tflops, "peak_tflops": fp32_peak, "frac": tflops / fp32_peak,
                      "flops_per_elem": FLOPS_PER_ELEM[("linear", "tangent")], "clock_mhz": mhz},
             "workload": "160^3 x 6 = 24,576,000 tets, 4,173,281 nodes, f32 vectors", "peak_kind": peak_kind}
@@ -767,8 +790,14 @@ def probe(a):
         y = torch.empty_like(v)
         arith = "f32" if a.vec == "f64" else None
 
+        if a.k > 0:
+            v = torch.randn((a.k, mesh.n_dofs), device="cuda", dtype=dt)
+            y = torch.empty_like(v)
+
         def op():
-            if a.op == "tangent":
+            if a.k > 0:
+                P.pfem_tangent_apply_multi(mesh, v, y)
+            elif a.op == "tangent":
                 P.pfem_tangent_apply(mesh, u, v, y, arith=arith)
             else:
                 P.pfem_residual(mesh, u, y, arith=arith)
@@ -779,7 +808,7 @@ def probe(a):
             op()
         ev[1].record()
         ev[1].synchronize()
-        out.update({"apply_us": ev[0].elapsed_time(ev[1]) * 1e3 / a.reps, "op": a.op})
+        out.update({"apply_us": ev[0].elapsed_time(ev[1]) * 1e3 / a.reps, "op": a.op, "k": a.k})
     else:
         P.pfem_set_solver_mode(MODES[a.solver_mode])
         P.pfem_solve_linear(mesh, tol=TOL, max_iter=a.max_iter, raise_on_error=False)

@@ -157,6 +157,19 @@ pfem_status pfem_residual(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, voi
 pfem_status pfem_tangent_apply(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, const void* v,
                                void* y);
 
+/* y_j = A v_j for k vectors at once (several load cases on one mesh: the six unit strains of
+ * Sec. "Three-dimensional solid mechanics homogenization", or independent solves sharing each
+ * operator application). The element data is read once per group of six vectors instead of
+ * once per vector, and pairs of vectors share one FP32x2 instruction stream. v, y: k vectors
+ * of n_dofs each, vector j starting at element j * n_dofs (float for PFEM_F32, double for
+ * PFEM_F64_F32; the element arithmetic is FP32 for both). Linear material only (u is ignored
+ * and may be NULL); Neo-Hookean meshes and other dtypes return PFEM_ERR_UNSUPPORTED; k < 0 or
+ * NULL vectors PFEM_ERR_INVALID_ARG; k = 0 does nothing. Dirichlet handling as in
+ * pfem_tangent_apply. Uses the mesh's scratch: do not overlap with other calls on the mesh.
+ * Asynchronous. */
+pfem_status pfem_tangent_apply_multi(pfem_mesh_t mesh, pfem_dtype dtype, const void* u, int32_t k, const void* v,
+                                     void* y);
+
 /* Same result as pfem_tangent_apply, for callers that cannot allocate device memory when
  * they apply the operator (a frozen or exhausted memory pool, code running inside allocator
  * callbacks, runtimes that only own memory handed to them up front). The paper has no

@@ -36,5 +36,6 @@ from .api import (  # noqa: F401
     pfem_solve_linear,
     pfem_solve_newton,
     pfem_tangent_apply,
+    pfem_tangent_apply_multi,
     pfem_version,
 )

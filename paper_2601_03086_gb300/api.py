@@ -150,6 +150,19 @@ def pfem_tangent_apply(mesh, u, v, y=None, arith=None):
     return y
 
 
+def pfem_tangent_apply_multi(mesh, v, y=None, arith=None):
+    """y[j] = A v[j] for the rows of v ((k, n_dofs) float32, or float64 with FP32 arithmetic)."""
+    if v.dim() != 2 or v.shape[1] != mesh.n_dofs or not v.is_contiguous() or not v.is_cuda:
+        raise ValueError("v must be a contiguous CUDA tensor of shape (k, %d)" % mesh.n_dofs)
+    y = torch.empty_like(v) if y is None else y
+    if y.shape != v.shape or not y.is_contiguous() or y.dtype != v.dtype:
+        raise ValueError("y must match v")
+    dt = PFEM_F32 if v.dtype == torch.float32 else _lib.PFEM_F64_F32
+    check(lib().pfem_tangent_apply_multi(mesh.handle, dt, None, int(v.shape[0]), C.c_void_p(v.data_ptr()),
+                                         C.c_void_p(y.data_ptr())))
+    return y
+
+
 def _scalar(s, like, name):
     """Device pointer of a one-entry tensor of the vector type (None = 1)."""
     if s is None:
