@@ -237,6 +237,32 @@ pfem_status pfem_solve_newton(pfem_mesh_t mesh, pfem_dtype dtype, const double* 
                               int32_t n_load_steps, int32_t max_newton, double inner_tol,
                               double* u_out, pfem_solve_info* info);
 
+/* k independent linear solves on one mesh that share every operator application (several
+ * load cases: App. B K u = f per case; the six unit-strain cases of the homogenisation
+ * appendix): solves P (K + S) P x_j = P b_j by Jacobi-PCG for j < k, where S is the mesh's
+ * penalty-spring matrix (zero without springs), with x_j = 0 on prescribed DOFs. b, u0, u_out:
+ * k vectors of n_dofs FP64 device values each, vector j at element j * n_dofs (u0 NULL = zero
+ * start; u0 and u_out may alias). Per solve: stops when ||P (b_j - A x_j)|| / ||P b_j|| < tol
+ * (checked before the first iteration, confirmed with the FP64 operator), at most max_iter
+ * iterations. dtype: PFEM_F32 = FP32 element arithmetic in one multi-vector element pass per
+ * iteration, FP64 vectors, dots and residual replacements; PFEM_F64 = FP64 element arithmetic.
+ * infos: k entries (may be NULL). Linear material only. Returns the first failing status
+ * (NOT_CONVERGED, NONFINITE) or PFEM_OK when every solve converged. */
+pfem_status pfem_solve_linear_multi(pfem_mesh_t mesh, pfem_dtype dtype, int32_t k, const double* b,
+                                    const double* u0, double tol, int32_t max_iter, double* u_out,
+                                    pfem_solve_info* infos);
+
+/* Penalty springs between node pairs (the homogenisation appendix's "virtual elements" that
+ * couple corresponding nodes of opposite faces of a periodic cell): energy 1/2 kappa
+ * |u_a - u_b|^2 per pair. pairs: HOST array of n_pairs (a, b) node ids; stiffness kappa >= 0;
+ * n_pairs = 0 removes them. Replaces any earlier set; synchronises the mesh stream. With
+ * springs, pfem_tangent_apply(_multi), pfem_residual, pfem_jacobi_diag and the linear solvers
+ * use K + S (pfem_solve_linear then needs zero prescribed values and load scale 1); the energy,
+ * its autograd entry points, batches, the no-alloc apply and Newton return
+ * PFEM_ERR_UNSUPPORTED. Errors: INVALID_ARG (ids out of range or equal, kappa < 0 or not
+ * finite), OUT_OF_MEMORY / CUDA. */
+pfem_status pfem_mesh_set_springs(pfem_mesh_t mesh, int64_t n_pairs, const int32_t* pairs, double stiffness);
+
 /* Solver loop style for later solves (process-wide); every mode gives bitwise identical
  * iterates. 0: one persistent cooperative kernel runs PCG iterations until an FP64
  * residual replacement or termination (grid barriers with bounded waits: a barrier that

@@ -28,12 +28,14 @@ from .api import (  # noqa: F401
     pfem_mesh_create,
     pfem_mesh_destroy,
     pfem_mesh_set_load_scale,
+    pfem_mesh_set_springs,
     pfem_plan_check,
     pfem_residual,
     pfem_set_barrier_test,
     pfem_set_kernel_timing,
     pfem_set_solver_mode,
     pfem_solve_linear,
+    pfem_solve_linear_multi,
     pfem_solve_newton,
     pfem_tangent_apply,
     pfem_tangent_apply_multi,

@@ -105,6 +105,9 @@ SIGNATURES = {
     "pfem_solve_newton": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_double, C.c_int32, C.c_int32,
                                       C.c_double, C.c_void_p, C.POINTER(SolveInfo)]),
     "pfem_set_solver_mode": (C.c_int32, [C.c_int32]),
+    "pfem_solve_linear_multi": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_double,
+                                            C.c_int32, C.c_void_p, C.c_void_p]),
+    "pfem_mesh_set_springs": (C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_double]),
     "pfem_set_kernel_timing": (C.c_int32, [C.c_int32]),
     "pfem_set_barrier_test": (C.c_int32, [C.c_int64, C.c_int32]),
     "pfem_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),

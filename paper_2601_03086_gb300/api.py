@@ -236,6 +236,35 @@ def pfem_solve_newton(mesh, u0=None, tol=1e-8, n_load_steps=1, max_newton=50, in
     return u_out, _info_dict(info)
 
 
+def pfem_solve_linear_multi(mesh, b, u0=None, tol=1e-8, max_iter=100000, precision="f32", u_out=None,
+                            raise_on_error=True):
+    """k independent Jacobi-PCG solves sharing each operator application; b: (k, n_dofs)
+    float64 CUDA tensor. Returns (u (k, n_dofs) float64, list of k info dicts)."""
+    if b.dim() != 2 or b.shape[1] != mesh.n_dofs or b.dtype != torch.float64 or not b.is_contiguous():
+        raise ValueError("b must be a contiguous float64 CUDA tensor of shape (k, %d)" % mesh.n_dofs)
+    k = int(b.shape[0])
+    u_out = torch.empty_like(b) if u_out is None else u_out
+    u0p = None
+    if u0 is not None:
+        if u0.shape != b.shape or u0.dtype != torch.float64 or not u0.is_contiguous():
+            raise ValueError("u0 must match b")
+        u0p = C.c_void_p(u0.data_ptr())
+    infos = (_lib.SolveInfo * k)()
+    st = lib().pfem_solve_linear_multi(mesh.handle, PFEM_F32 if precision == "f32" else PFEM_F64, k,
+                                       C.c_void_p(b.data_ptr()), u0p, float(tol), int(max_iter),
+                                       C.c_void_p(u_out.data_ptr()), infos)
+    if raise_on_error:
+        check(st)
+    return u_out, [_info_dict(i) for i in infos]
+
+
+def pfem_mesh_set_springs(mesh, pairs, stiffness):
+    """Penalty springs between node pairs ((n, 2) int array; empty removes them)."""
+    pairs = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    check(lib().pfem_mesh_set_springs(mesh.handle, int(pairs.shape[0]), _ptr(pairs) if pairs.size else None,
+                                      float(stiffness)))
+
+
 def pfem_set_solver_mode(mode):
     check(lib().pfem_set_solver_mode(int(mode)))
 

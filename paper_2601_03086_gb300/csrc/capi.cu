@@ -315,6 +315,7 @@ void pfem_mesh_destroy(pfem_mesh_t m) {
   }
   cudaStreamSynchronize(m->stream);
   solver_release(m);
+  springs_release(m);
   cudaFree(m->arena);
   cudaFreeHost(m->host_out);
   delete m;
@@ -343,6 +344,14 @@ pfem_status pfem_mesh_set_load_scale(pfem_mesh_t m, double s) {
   return PFEM_OK;
 }
 
+static pfem_status no_springs(pfem_mesh_t m, const char* what) {
+  if (m->n_spring_nodes) {
+    set_error("%s does not include penalty springs; remove them with pfem_mesh_set_springs(mesh, 0, NULL, 0)", what);
+    return PFEM_ERR_UNSUPPORTED;
+  }
+  return PFEM_OK;
+}
+
 static pfem_status op_common(pfem_mesh_t m, pfem_dtype dt) {
   pfem_status st = check_mesh(m);
   if (st) return st;
@@ -359,7 +368,7 @@ static pfem_dtype ct_of(pfem_dtype d) { return d == PFEM_F64 ? PFEM_F64 : PFEM_F
 
 pfem_status pfem_energy(pfem_mesh_t m, pfem_dtype dt, const void* u, double* energy, double* strain_energy) {
   pfem_status st = op_common(m, dt);
-  if (st) return st;
+  if (st || (st = no_springs(m, "pfem_energy"))) return st;
   if (!u) {
     set_error("u is NULL");
     return PFEM_ERR_INVALID_ARG;
@@ -390,7 +399,8 @@ pfem_status pfem_residual(pfem_mesh_t m, pfem_dtype dt, const void* u, void* r) 
     return PFEM_ERR_INVALID_ARG;
   }
   OpArgs a{u, nullptr, nullptr, r, nullptr, m->load_scale};
-  return launch_element_op(m->plan, OP_RESIDUAL, vt_of(dt), ct_of(dt), a, m->stream);
+  if ((st = launch_element_op(m->plan, OP_RESIDUAL, vt_of(dt), ct_of(dt), a, m->stream))) return st;
+  return springs_apply(m, vt_of(dt), 1, u, r, m->stream);
 }
 
 pfem_status pfem_tangent_apply(pfem_mesh_t m, pfem_dtype dt, const void* u, const void* v, void* y) {
@@ -401,12 +411,13 @@ pfem_status pfem_tangent_apply(pfem_mesh_t m, pfem_dtype dt, const void* u, cons
     return PFEM_ERR_INVALID_ARG;
   }
   OpArgs a{u, v, y, nullptr, nullptr, m->load_scale};
-  return launch_element_op(m->plan, OP_TANGENT, vt_of(dt), ct_of(dt), a, m->stream);
+  if ((st = launch_element_op(m->plan, OP_TANGENT, vt_of(dt), ct_of(dt), a, m->stream))) return st;
+  return springs_apply(m, vt_of(dt), 1, v, y, m->stream);
 }
 
 pfem_status pfem_energy_gradient(pfem_mesh_t m, pfem_dtype dt, const void* u, const void* scale, void* g) {
   pfem_status st = op_common(m, dt);
-  if (st) return st;
+  if (st || (st = no_springs(m, "pfem_energy_gradient"))) return st;
   if (!u || !g) {
     set_error("u/g is NULL");
     return PFEM_ERR_INVALID_ARG;
@@ -419,7 +430,7 @@ pfem_status pfem_energy_gradient(pfem_mesh_t m, pfem_dtype dt, const void* u, co
 pfem_status pfem_energy_hvp(pfem_mesh_t m, pfem_dtype dt, const void* u, const void* v, const void* scale,
                             void* y) {
   pfem_status st = op_common(m, dt);
-  if (st) return st;
+  if (st || (st = no_springs(m, "pfem_energy_hvp"))) return st;
   if (!v || !y || (m->plan.kind == PFEM_NEOHOOKEAN && !u)) {
     set_error("u/v/y is NULL");
     return PFEM_ERR_INVALID_ARG;
@@ -448,7 +459,8 @@ pfem_status pfem_jacobi_diag(pfem_mesh_t m, pfem_dtype dt, const void* u, void* 
     return PFEM_ERR_INVALID_ARG;
   }
   OpArgs a{u, nullptr, nullptr, nullptr, d, m->load_scale};
-  return launch_element_op(m->plan, OP_DIAG, vt_of(dt), ct_of(dt), a, m->stream);
+  if ((st = launch_element_op(m->plan, OP_DIAG, vt_of(dt), ct_of(dt), a, m->stream))) return st;
+  return springs_diag(m, vt_of(dt), d, m->stream);
 }
 
 }  // extern "C"

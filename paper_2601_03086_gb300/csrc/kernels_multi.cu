@@ -160,6 +160,11 @@ static pfem_status run_multi(const DevPlan& P, const void* v, void* y, int k, cu
   return PFEM_OK;
 }
 
+pfem_status launch_multi_apply(const DevPlan& P, pfem_dtype vt, int k, const void* v, void* y, cudaStream_t s) {
+  if (vt == PFEM_F32) return P.dim == 3 ? run_multi<3, float>(P, v, y, k, s) : run_multi<2, float>(P, v, y, k, s);
+  return P.dim == 3 ? run_multi<3, double>(P, v, y, k, s) : run_multi<2, double>(P, v, y, k, s);
+}
+
 }  // namespace pfem
 
 using namespace pfem;
@@ -182,7 +187,7 @@ extern "C" pfem_status pfem_tangent_apply_multi(pfem_mesh_t m, pfem_dtype dt, co
     return PFEM_ERR_INVALID_ARG;
   }
   if (k == 0) return PFEM_OK;
-  const DevPlan& P = m->plan;
-  if (dt == PFEM_F32) return P.dim == 3 ? run_multi<3, float>(P, v, y, k, m->stream) : run_multi<2, float>(P, v, y, k, m->stream);
-  return P.dim == 3 ? run_multi<3, double>(P, v, y, k, m->stream) : run_multi<2, double>(P, v, y, k, m->stream);
+  const pfem_dtype vt = dt == PFEM_F32 ? PFEM_F32 : PFEM_F64;
+  if ((st = launch_multi_apply(m->plan, vt, k, v, y, m->stream))) return st;
+  return springs_apply(m, vt, k, v, y, m->stream);
 }

@@ -366,6 +366,16 @@ constexpr int64_t kDeferHaloPartials = 1 << 18;
 // (noalloc.cu); the first call per device loads the array's module. pfem_mesh_create calls it.
 pfem_status noalloc_scratch(void** out);
 
+// Multi-right-hand-side linear tangent action y_j = A v_j (kernels_multi.cu); vt = PFEM_F32
+// (float vectors) or PFEM_F64 (double vectors), FP32 element arithmetic.
+pfem_status launch_multi_apply(const DevPlan& P, pfem_dtype vt, int k, const void* v, void* y, cudaStream_t s);
+
+// Penalty springs of a mesh (springs.cu): y_j += S v_j on free DOFs (v read as 0 on prescribed
+// DOFs) for k vectors of the vector type vt; d += diag S on free DOFs. No-ops without springs.
+pfem_status springs_apply(pfem_mesh_t m, pfem_dtype vt, int k, const void* v, void* y, cudaStream_t s);
+pfem_status springs_diag(pfem_mesh_t m, pfem_dtype vt, void* d, cudaStream_t s);
+void springs_release(pfem_mesh_t m);
+
 // Dynamic shared memory one tile CTA of launch_element_op needs.
 size_t element_op_smem(const DevPlan& P, int ops, pfem_dtype ct);
 
@@ -395,4 +405,12 @@ struct pfem_mesh_s {
   int32_t* host_int = nullptr;      // pinned, 4 ints
   int64_t n_dofs = 0, n_free = 0;
   void* solver = nullptr;          // solver workspace (solve.cu), created on first solve
+  // penalty springs ("virtual elements" between node pairs, springs.cu): per node with
+  // springs its partners in ascending id order (CSR), one stiffness for all
+  int32_t n_spring_nodes = 0;
+  int32_t* spring_node = nullptr;    // device, n_spring_nodes ids (ascending)
+  int32_t* spring_ptr = nullptr;     // device, n_spring_nodes + 1
+  int32_t* spring_partner = nullptr; // device
+  void* spring_block = nullptr;      // one allocation holding the three arrays
+  double spring_k = 0.0;
 };

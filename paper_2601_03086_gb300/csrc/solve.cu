@@ -21,6 +21,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "kernels_vec.cuh"
 #include "pfem_internal.h"
@@ -374,6 +375,28 @@ static pfem_status status_of(int done) {
   }
 }
 
+pfem_status solve_multi_core(pfem_mesh_t m, pfem_dtype dt, int k, const double* b, const double* u0, double tol,
+                             int max_iter, double* u_out, pfem_solve_info* infos);
+
+// A linear solve on a mesh with penalty springs: the multi-solve path with one right-hand
+// side b = s f_ext (prescribed values must be zero there: no lifting of nonzero values).
+static pfem_status solve_with_springs(pfem_mesh_t m, pfem_dtype dt, const double* u0, double tol, int max_iter,
+                                      double* u_out, pfem_solve_info* info) {
+  if (m->load_scale != 1.0) {
+    set_error("meshes with penalty springs solve at load scale 1 only");
+    return PFEM_ERR_UNSUPPORTED;
+  }
+  std::vector<double> v((size_t)m->n_dofs);
+  PFEM_CUDA(cudaMemcpy(v.data(), m->plan.dvalues, v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+  for (double x : v)
+    if (x != 0.0) {
+      set_error("meshes with penalty springs need zero prescribed values");
+      return PFEM_ERR_UNSUPPORTED;
+    }
+  pfem_solve_info tmp;
+  return solve_multi_core(m, dt, 1, m->plan.f_ext, u0, tol, max_iter, u_out, info ? info : &tmp);
+}
+
 }  // namespace pfem
 
 using namespace pfem;
@@ -420,6 +443,7 @@ pfem_status pfem_solve_linear(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
     set_error("invalid solve arguments");
     return PFEM_ERR_INVALID_ARG;
   }
+  if (m->n_spring_nodes) return solve_with_springs(m, dt, u0, tol, max_iter, u_out, info);
   SolverWS* w;
   const int64_t launches0 = g_kernel_launches;
   if ((st = ws_get(m, &w))) return st;
@@ -459,6 +483,10 @@ pfem_status pfem_solve_newton(pfem_mesh_t m, pfem_dtype dt, const double* u0, do
       (dt != PFEM_F32 && dt != PFEM_F64)) {
     set_error("invalid Newton arguments");
     return PFEM_ERR_INVALID_ARG;
+  }
+  if (m->n_spring_nodes) {
+    set_error("pfem_solve_newton does not include penalty springs");
+    return PFEM_ERR_UNSUPPORTED;
   }
   SolverWS* w;
   const int64_t launches0 = g_kernel_launches;

@@ -44,4 +44,7 @@ from .problems import (  # noqa: F401
     smooth_shape,
     make_warm_start,
     random_field,
+    periodic_pairs,
+    tpms_cell,
+    laminate_cell,
 )

@@ -350,3 +350,91 @@ def random_field(problem, seed, std=0.01, zero_masked=True):
     if zero_masked:
         u[problem["dirichlet_mask"].astype(bool)] = 0.0
     return u
+
+
+# ---------------------------------------------------------------------------------------
+# Periodic unit cells for the homogenisation (synthetic TPMS geometry)
+# ---------------------------------------------------------------------------------------
+
+_TPMS = {
+    # level-set functions phi(x, y, z) of the triply periodic minimal surfaces of the TPMS
+    # appendix (unit period)
+    "primitive": lambda x, y, z: np.cos(2 * np.pi * x) + np.cos(2 * np.pi * y) + np.cos(2 * np.pi * z),
+    "gyroid": lambda x, y, z: (np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) + np.sin(2 * np.pi * y) *
+                               np.cos(2 * np.pi * z) + np.sin(2 * np.pi * z) * np.cos(2 * np.pi * x)),
+    "diamond": lambda x, y, z: (np.cos(2 * np.pi * x) * np.cos(2 * np.pi * y) * np.cos(2 * np.pi * z) -
+                                np.sin(2 * np.pi * x) * np.sin(2 * np.pi * y) * np.sin(2 * np.pi * z)),
+    "fischer_koch_s": lambda x, y, z: (np.cos(4 * np.pi * x) * np.sin(2 * np.pi * y) * np.cos(2 * np.pi * z) +
+                                       np.cos(2 * np.pi * x) * np.cos(4 * np.pi * y) * np.sin(2 * np.pi * z) +
+                                       np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) * np.cos(4 * np.pi * z)),
+}
+
+
+def periodic_pairs(n):
+    """Node pairs (a, b) of opposite faces of the n^3-hex unit cell (lexicographic nodes, x
+    fastest): (0, j, k)-(n, j, k), (i, 0, k)-(i, n, k), (i, j, 0)-(i, j, n) for all indices,
+    so edge and corner nodes are chained around the cell (ring-type coupling)."""
+    s = n + 1
+    idx = np.arange(s)
+    a, b = [], []
+    J, K = np.meshgrid(idx, idx, indexing="ij")
+    for axis in range(3):
+        if axis == 0:
+            lo, hi = 0 + s * J + s * s * K, n + s * J + s * s * K
+        elif axis == 1:
+            lo, hi = J + 0 * s + s * s * K, J + n * s + s * s * K
+        else:
+            lo, hi = J + s * K + 0, J + s * K + s * s * n
+        a.append(lo.ravel())
+        b.append(hi.ravel())
+    return np.stack([np.concatenate(a), np.concatenate(b)], axis=1).astype(np.int32)
+
+
+def tpms_cell(n, family="gyroid", c=0.0, network="solid", E_solid=1.0, nu=0.3, void_ratio=1e-3):
+    """Periodic TPMS unit cell [0,1]^3 as an n^3 voxel grid split into 6 Kuhn tets per voxel.
+
+    A voxel is solid where the level set at its centre satisfies phi > c (solid network) or
+    -c <= phi <= c (sheet network); solid voxels get E_solid, void voxels void_ratio * E_solid
+    (a soft phase keeps the operator definite; the appendix's void has E = 0), nu everywhere.
+    Node 0 (the origin) is fixed in all DOFs (removes the rigid translations left by the
+    periodic coupling); no traction. Returns the problem dict with the extra keys "pairs"
+    (periodic node pairs), "solid" (per-element bool) and "volume_fraction"."""
+    h = 1.0 / n
+    centres = (np.arange(n) + 0.5) * h
+    X, Y, Z = np.meshgrid(centres, centres, centres, indexing="ij")
+    phi = _TPMS[family](X, Y, Z)
+    solid_vox = phi > c if network == "solid" else np.abs(phi) <= c
+    coords, conn = grid_tet(n, n, n)
+    i, j, k = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    vox = solid_vox[i.ravel(order="F"), j.ravel(order="F"), k.ravel(order="F")]
+    solid = np.repeat(vox, 6)
+    E = np.where(solid, E_solid, void_ratio * E_solid)
+    nuv = np.full(conn.shape[0], nu)
+    mask = np.zeros(coords.shape, dtype=np.uint8)
+    mask[0, :] = 1
+    p = _problem(3, coords, conn, "linear", E, nuv, mask, np.zeros(coords.shape), np.zeros((0, 3), np.int32),
+                 np.zeros((0, 3)), f"tpms_{family}_{network}_{n}^3", 0)
+    p["pairs"] = periodic_pairs(n)
+    p["solid"] = solid
+    p["volume_fraction"] = float(vox.mean())
+    return p
+
+
+def laminate_cell(n, layers=(1.0, 5.0), nus=(0.3, 0.2), axis=0):
+    """Periodic laminate on the n^3 grid: voxel slabs perpendicular to `axis` alternate
+    between the phases (Young's moduli `layers`, Poisson's ratios `nus`) with n / len(layers)
+    voxels each; node 0 fixed, periodic pairs as in tpms_cell."""
+    coords, conn = grid_tet(n, n, n)
+    i, j, k = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    coord = (i, j, k)[axis].ravel(order="F")
+    m = len(layers)
+    phase = np.repeat((coord * m) // n, 6)
+    E = np.asarray(layers, dtype=np.float64)[phase]
+    nuv = np.asarray(nus, dtype=np.float64)[phase]
+    mask = np.zeros(coords.shape, dtype=np.uint8)
+    mask[0, :] = 1
+    p = _problem(3, coords, conn, "linear", E, nuv, mask, np.zeros(coords.shape), np.zeros((0, 3), np.int32),
+                 np.zeros((0, 3)), f"laminate_{n}^3", 0)
+    p["pairs"] = periodic_pairs(n)
+    p["phase_fraction"] = [float(np.mean(phase == q)) for q in range(m)]
+    return p
