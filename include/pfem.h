@@ -252,6 +252,24 @@ pfem_status pfem_solve_linear_multi(pfem_mesh_t mesh, pfem_dtype dtype, int32_t 
                                     const double* u0, double tol, int32_t max_iter, double* u_out,
                                     pfem_solve_info* infos);
 
+/* Effective elastic tensor of a periodic cell (appendix "Numerical homogenization theory",
+ * with the TPMS cells of appendix "Generation of TPMS geometries" as typical input): for the
+ * six unit strains eps0 (11, 22, 33, 12, 13, 23; shear cases with both off-diagonal entries
+ * 1, as printed) the fluctuation X^v solves (K + S) X^v = K X^0 with X^0 = eps0 (X - X_min)
+ * and S the mesh's penalty springs between opposite-face nodes (pfem_mesh_set_springs), by
+ * six PCG solves sharing each operator pass; then E^H = X^T K X / |Omega| with X = X^0 - X^v
+ * (the appendix's integral of (eps0 - eps^v) : E : (eps0 - eps^v)); |Omega| is the volume of
+ * the coordinates' bounding box. The mesh must fix every DOF of one node at the cell's minimum
+ * corner (the periodic coupling leaves rigid translations free) and have no other prescribed
+ * DOFs. coords: HOST n_nodes*3 reference coordinates (those the mesh was built from). xv0:
+ * optional warm start of the six fluctuations (device, 6 * n_dofs FP64, NULL = zero: the
+ * Sec. "Warm-start" use). eh: HOST 36 doubles, row-major E^H. xv_out: optional device
+ * 6 * n_dofs FP64 output of the fluctuations. infos: 6 entries (may be NULL). dtype selects the
+ * element arithmetic of the solves (PFEM_F32 / PFEM_F64); loads and E^H use FP64. Returns
+ * PFEM_ERR_NOT_CONVERGED (E^H still written) if a solve stopped at max_iter. Synchronises. */
+pfem_status pfem_homogenize(pfem_mesh_t mesh, pfem_dtype dtype, const double* coords, const double* xv0, double tol,
+                            int32_t max_iter, double* eh, double* xv_out, pfem_solve_info* infos);
+
 /* Penalty springs between node pairs (the homogenisation appendix's "virtual elements" that
  * couple corresponding nodes of opposite faces of a periodic cell): energy 1/2 kappa
  * |u_a - u_b|^2 per pair. pairs: HOST array of n_pairs (a, b) node ids; stiffness kappa >= 0;

@@ -24,6 +24,7 @@ from .api import (  # noqa: F401
     pfem_energy,
     pfem_energy_gradient,
     pfem_energy_hvp,
+    pfem_homogenize,
     pfem_jacobi_diag,
     pfem_mesh_create,
     pfem_mesh_destroy,

@@ -108,6 +108,8 @@ SIGNATURES = {
     "pfem_solve_linear_multi": (C.c_int32, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_double,
                                             C.c_int32, C.c_void_p, C.c_void_p]),
     "pfem_mesh_set_springs": (C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_double]),
+    "pfem_homogenize": (C.c_int32, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_double, C.c_int32, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
     "pfem_set_kernel_timing": (C.c_int32, [C.c_int32]),
     "pfem_set_barrier_test": (C.c_int32, [C.c_int64, C.c_int32]),
     "pfem_batch_create": (C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),

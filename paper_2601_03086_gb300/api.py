@@ -265,6 +265,25 @@ def pfem_mesh_set_springs(mesh, pairs, stiffness):
                                       float(stiffness)))
 
 
+def pfem_homogenize(mesh, coords, xv0=None, tol=1e-8, max_iter=100000, precision="f32", raise_on_error=True):
+    """Effective tensor of a periodic cell (springs set on the mesh). Returns (E^H 6x6 numpy,
+    fluctuations (6, n_dofs) float64 CUDA tensor, list of 6 info dicts)."""
+    xyz = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1)
+    eh = np.zeros(36)
+    xv = torch.empty((6, mesh.n_dofs), dtype=torch.float64, device="cuda")
+    xv0p = None
+    if xv0 is not None:
+        if xv0.shape != xv.shape or xv0.dtype != torch.float64 or not xv0.is_contiguous():
+            raise ValueError("xv0 must be a contiguous float64 CUDA tensor of shape (6, %d)" % mesh.n_dofs)
+        xv0p = C.c_void_p(xv0.data_ptr())
+    infos = (_lib.SolveInfo * 6)()
+    st = lib().pfem_homogenize(mesh.handle, PFEM_F32 if precision == "f32" else PFEM_F64, _ptr(xyz), xv0p,
+                               float(tol), int(max_iter), _ptr(eh), C.c_void_p(xv.data_ptr()), infos)
+    if raise_on_error:
+        check(st)
+    return eh.reshape(6, 6), xv, [_info_dict(i) for i in infos]
+
+
 def pfem_set_solver_mode(mode):
     check(lib().pfem_set_solver_mode(int(mode)))
 

@@ -79,3 +79,67 @@ def test_multi_apply_large_cube_sampled_rows():
         ys = fem.tangent_apply(ms, None, v[j].astype(np.float64).reshape(-1, 3)[used].reshape(-1)).reshape(-1, 3)
         assert rel_l2(y[j][nodes], ys[pos]) <= 1e-5, j
     mesh.close()
+
+
+def test_multi_solve_matches_oracle_per_load_case():
+    """Four load cases on the 12^3 lognormal cube solved together (FP32 and FP64 element
+    arithmetic): each solution within 1e-6 of the oracle's, iterations within the FP32 bar of
+    the oracle's Jacobi-PCG, every true residual below tol."""
+    from oracle import solve
+
+    P = pfem()
+    p = pi.cube_problem(12, seed=9)
+    m = fem.Mesh(p)
+    K = fem.assemble_linear_K(m)
+    free = ~m.mask
+    rng = np.random.default_rng(21)
+    k = 4
+    B = rng.standard_normal((k, m.n_dofs)) * free
+    mesh = P.Mesh(p)
+    for precision in ("f32", "f64"):
+        U, infos = P.pfem_solve_linear_multi(mesh, torch.tensor(B, device="cuda"), tol=1e-8, precision=precision)
+        U = host(U).reshape(k, -1)
+        Kff = K[free][:, free].tocsr()
+        for j in range(k):
+            ref = np.linalg.norm(B[j][free])
+            x, it = solve.pcg(Kff, B[j][free], np.zeros(int(free.sum())), Kff.diagonal(), 1e-8, ref, 100000)
+            u_ref = np.zeros(m.n_dofs)
+            u_ref[free] = x
+            assert rel_l2(U[j], u_ref) <= 1e-6, (precision, j)
+            bar = 2 if precision == "f64" else max(2, int(0.015 * it))
+            assert abs(infos[j]["iterations"] - it) <= bar, (precision, j, infos[j], it)
+            assert infos[j]["rel_residual_true_f64"] < 1e-8
+    mesh.close()
+
+
+def test_springs_in_operator_and_diagonal():
+    """Penalty springs between random node pairs: tangent, multi tangent and Jacobi diagonal
+    equal the oracle's K + S (prescribed rows keep the identity)."""
+    from oracle import homog
+
+    P = pfem()
+    p = pi.cube_problem(6, seed=4)
+    m = fem.Mesh(p)
+    rng = np.random.default_rng(3)
+    pairs = rng.choice(p["coords"].shape[0], size=(40, 2), replace=False).astype(np.int32)
+    kappa = 7.5
+    A = (fem.assemble_linear_K(m) + homog.spring_matrix(m.n_dofs, pairs, kappa)).tocsr()
+    free = (~m.mask).astype(np.float64)
+    mesh = P.Mesh(p)
+    P.pfem_mesh_set_springs(mesh, pairs, kappa)
+    v = rng.standard_normal((2, m.n_dofs))
+    for j in range(2):
+        y_ref = free * (A @ (free * v[j])) + (1 - free) * v[j]
+        y = host(P.pfem_tangent_apply(mesh, None, dev(v[j])))
+        assert rel_l2(y, y_ref) <= 1e-12
+    ym = host(P.pfem_tangent_apply_multi(mesh, torch.tensor(v, dtype=torch.float32, device="cuda"))).reshape(2, -1)
+    for j in range(2):
+        y_ref = free * (A @ (free * v[j].astype(np.float32))) + (1 - free) * v[j].astype(np.float32)
+        assert rel_l2(ym[j], y_ref) <= 1e-5
+    d = host(P.pfem_jacobi_diag(mesh, dtype=torch.float64))
+    assert rel_l2(d, free * A.diagonal() + (1 - free)) <= 1e-12
+    P.pfem_mesh_set_springs(mesh, np.zeros((0, 2), np.int32), 0.0)  # removed again
+    y0 = host(P.pfem_tangent_apply(mesh, None, dev(v[0])))
+    K = fem.assemble_linear_K(m)
+    assert rel_l2(y0, free * (K @ (free * v[0])) + (1 - free) * v[0]) <= 1e-12
+    mesh.close()
