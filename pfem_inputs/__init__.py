@@ -48,3 +48,4 @@ from .problems import (  # noqa: F401
     tpms_cell,
     laminate_cell,
 )
+from .quads import cook_membrane, nh_beam, quad_grid, quad_problem  # noqa: F401
