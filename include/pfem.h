@@ -126,6 +126,19 @@ typedef struct {
 pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem_mesh_t* out);
 void pfem_mesh_destroy(pfem_mesh_t mesh);
 
+/* Plane-strain quadrilateral mesh (Sec. "Nonlinear hyperelasticity": the Q4 beam and Q8 Cook
+ * membrane): desc->dim = 2, desc->conn holds n_elems * npe node ids per element, npe = 4
+ * (bilinear, corners counterclockwise; 2 x 2 Gauss points) or 8 (serendipity: corners
+ * counterclockwise, then the mid-edge nodes of edges 0-1, 1-2, 2-3, 3-0; 3 x 3 Gauss points).
+ * Traction facets are element edges of npe == 4 ? 2 : 3 node ids (a, b[, mid]) with constant
+ * traction (consistent loads |e|/2 at each end, or |e| (1/6, 1/6, 2/3)). Materials, Dirichlet
+ * data and ownership as pfem_mesh_create. The mesh works with pfem_energy, pfem_residual,
+ * pfem_tangent_apply, pfem_jacobi_diag, the energy-gradient / Hessian entry points and the
+ * single-mesh solvers (graph and plain loops); the multi-vector, batch, no-alloc, persistent
+ * and serving paths are for simplex meshes (PFEM_ERR_UNSUPPORTED). Errors: INVALID_ARG,
+ * DEGENERATE_ELEMENT (det J <= 0 at a Gauss point, e.g. clockwise nodes), OUT_OF_MEMORY. */
+pfem_status pfem_mesh_create_quad(const pfem_mesh_desc* desc, int32_t npe, void* cuda_stream, pfem_mesh_t* out);
+
 /* Host-only: validate and plan desc exactly as pfem_mesh_create does, then check the plan's
  * structural invariants (every element in one tile, every incidence in one slot, complete
  * nodes holding all their incidences, halo nodes with one partial per touching tile).

@@ -250,3 +250,70 @@ def tangent_apply(m, u, v):
     free = (~m.mask).astype(np.float64)
     v = np.asarray(v, dtype=np.float64).reshape(-1)
     return free * (stiffness(m, u) @ (free * v)) + (1 - free) * v
+
+
+# ---------------------------------------------------------------------------------------
+# Solvers (the algorithms of oracle/solve.py on quadrilateral meshes)
+# ---------------------------------------------------------------------------------------
+
+
+def min_jacobian(m, u):
+    return min(float(np.linalg.det(F).min()) for F in deformation_gradients(m, u))
+
+
+def lifted(m, u, scale=1.0):
+    out = np.array(u, dtype=np.float64).reshape(-1).copy()
+    out[m.mask] = scale * m.values[m.mask]
+    return out
+
+
+def solve_linear(m, u0=None, tol=1e-8, max_iter=100000):
+    """Jacobi-PCG on K_ff u_f = f_f - K_fc u_c (oracle/solve.py's stopping rule)."""
+    from . import solve
+
+    K = stiffness(m)
+    u = lifted(m, np.zeros(m.n_dofs) if u0 is None else u0)
+    free = ~m.mask
+    Kff = K[free][:, free].tocsr()
+    b = external_force(m)[free] - K[free][:, m.mask] @ u[m.mask]
+    ref = float(np.linalg.norm(b)) or 1.0
+    x, it = solve.pcg(Kff, b, u[free], Kff.diagonal(), tol, ref, max_iter)
+    u[free] = x
+    return u, it
+
+
+def solve_newton(m, u0=None, tol=1e-8, n_load_steps=1, max_newton=50, inner_tol=1e-8):
+    """Newton-Raphson with load steps and halving on J <= 0 (oracle/solve.py's algorithm),
+    inner Jacobi-PCG to inner_tol. Returns (u, newton_iterations)."""
+    from . import solve
+
+    u = np.zeros(m.n_dofs) if u0 is None else np.array(u0, dtype=np.float64).reshape(-1).copy()
+    free = ~m.mask
+    n_newton = 0
+    for s in range(1, n_load_steps + 1):
+        scale = s / n_load_steps
+        u = lifted(m, u, scale)
+        r0 = residual(m, lifted(m, np.zeros(m.n_dofs), scale), scale)
+        ref = float(np.linalg.norm(r0)) or 1.0
+        for _ in range(max_newton + 1):
+            r = residual(m, u, scale)
+            if float(np.linalg.norm(r)) / ref <= tol:
+                break
+            K = stiffness(m, u)
+            Kff = K[free][:, free].tocsr()
+            rf = r[free]
+            d, _ = solve.pcg(Kff, -rf, np.zeros_like(rf), Kff.diagonal(), inner_tol, float(np.linalg.norm(rf)), 100000)
+            t = 1.0
+            for _ in range(11):
+                trial = u.copy()
+                trial[free] += t * d
+                if min_jacobian(m, trial) > 0.0:
+                    break
+                t *= 0.5
+            else:
+                raise FloatingPointError("inverted element in every trial step")
+            u = trial
+            n_newton += 1
+        else:
+            raise RuntimeError("Newton did not converge")
+    return u, n_newton

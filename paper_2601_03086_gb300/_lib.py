@@ -88,6 +88,7 @@ class SolveInfo(C.Structure):
 SIGNATURES = {
     "pfem_mesh_create": (C.c_int32, [C.POINTER(MeshDesc), C.c_void_p, C.POINTER(C.c_void_p)]),
     "pfem_mesh_destroy": (None, [C.c_void_p]),
+    "pfem_mesh_create_quad": (C.c_int32, [C.POINTER(MeshDesc), C.c_int32, C.c_void_p, C.POINTER(C.c_void_p)]),
     "pfem_plan_check": (C.c_int32, [C.POINTER(MeshDesc), C.POINTER(MeshStats)]),
     "pfem_mesh_stats_get": (C.c_int32, [C.c_void_p, C.POINTER(MeshStats)]),
     "pfem_mesh_set_load_scale": (C.c_int32, [C.c_void_p, C.c_double]),

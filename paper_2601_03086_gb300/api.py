@@ -41,6 +41,7 @@ def _dev(t, n, name):
 def _desc(problem):
     """MeshDesc plus the numpy arrays it points into (keep both alive during the call)."""
     dim = int(problem["dim"])
+    fn = 3 if int(problem.get("npe", 0)) == 8 else dim  # ids per traction facet
     arrays = dict(
         coords=np.ascontiguousarray(problem["coords"], dtype=np.float64),
         conn=np.ascontiguousarray(problem["conn"], dtype=np.int32),
@@ -48,7 +49,7 @@ def _desc(problem):
         mat_b=np.ascontiguousarray(problem["mat_b"], dtype=np.float64),
         mask=np.ascontiguousarray(problem["dirichlet_mask"], dtype=np.uint8),
         values=np.ascontiguousarray(problem["dirichlet_values"], dtype=np.float64),
-        facets=np.ascontiguousarray(problem["facets"], dtype=np.int32).reshape(-1, dim),
+        facets=np.ascontiguousarray(problem["facets"], dtype=np.int32).reshape(-1, fn),
         traction=np.ascontiguousarray(problem["traction"], dtype=np.float64).reshape(-1, dim),
         extra=None if problem.get("f_ext_extra") is None else np.ascontiguousarray(problem["f_ext_extra"],
                                                                                    dtype=np.float64),
@@ -91,7 +92,11 @@ class Mesh:
             stream = torch.cuda.current_stream()
         self.stream = stream
         h = C.c_void_p()
-        check(lib().pfem_mesh_create(C.byref(desc), C.c_void_p(stream.cuda_stream), C.byref(h)))
+        npe = int(problem.get("npe", 0))
+        if npe:  # quadrilaterals
+            check(lib().pfem_mesh_create_quad(C.byref(desc), npe, C.c_void_p(stream.cuda_stream), C.byref(h)))
+        else:
+            check(lib().pfem_mesh_create(C.byref(desc), C.c_void_p(stream.cuda_stream), C.byref(h)))
         self.handle = h
         self.dim = dim
         self.kind = problem["kind"]

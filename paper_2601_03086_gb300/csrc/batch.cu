@@ -35,8 +35,8 @@ pfem_status pfem_batch_create(const pfem_mesh_t* meshes, int32_t n, pfem_batch_t
       set_error("mesh %d is NULL", i);
       return PFEM_ERR_INVALID_ARG;
     }
-    if (meshes[i]->n_spring_nodes) {
-      set_error("mesh %d has penalty springs, which batches do not evaluate", i);
+    if (meshes[i]->n_spring_nodes || meshes[i]->plan.elem_npe) {
+      set_error("mesh %d has penalty springs or quadrilaterals, which batches do not evaluate", i);
       return PFEM_ERR_UNSUPPORTED;
     }
     if (meshes[i]->plan.dim != 3) {

@@ -178,8 +178,8 @@ extern "C" pfem_status pfem_tangent_apply_multi(pfem_mesh_t m, pfem_dtype dt, co
     set_error("pfem_tangent_apply_multi: dtype must be PFEM_F32 or PFEM_F64_F32 (FP32 element arithmetic)");
     return PFEM_ERR_UNSUPPORTED;
   }
-  if (m->plan.kind != PFEM_LINEAR) {
-    set_error("pfem_tangent_apply_multi: linear material only (use pfem_tangent_apply per vector)");
+  if (m->plan.kind != PFEM_LINEAR || m->plan.elem_npe) {
+    set_error("pfem_tangent_apply_multi: linear simplex meshes only (use pfem_tangent_apply per vector)");
     return PFEM_ERR_UNSUPPORTED;
   }
   if (k < 0 || (k > 0 && (!v || !y))) {

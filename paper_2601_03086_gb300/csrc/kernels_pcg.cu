@@ -563,8 +563,8 @@ pfem_status launch_pcg_persistent(const DevPlan& P, pfem_dtype ct, const Persist
     set_error("persistent PCG kernel runs FP32 element arithmetic only");
     return PFEM_ERR_UNSUPPORTED;
   }
-  if (P.n_tiles < 1) {
-    set_error("persistent PCG kernel: empty plan");
+  if (P.n_tiles < 1 || P.elem_npe) {
+    set_error("persistent PCG kernel: empty plan or quadrilateral mesh");
     return PFEM_ERR_UNSUPPORTED;
   }
   // one resident CTA per tile where the whole mesh fits on the GPU at once, else CTAs that

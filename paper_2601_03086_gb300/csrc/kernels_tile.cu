@@ -288,6 +288,7 @@ static pfem_status dispatch_kind(const DevPlan& P, int ops, const OpArgs& A, cud
 
 pfem_status launch_element_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dtype ct, const OpArgs& a,
                               cudaStream_t s) {
+  if (P.elem_npe) return launch_quad_op(P, ops, vt, ct, a, s);
   if (vt == PFEM_F32 && ct == PFEM_F32) return dispatch_kind<float, float>(P, ops, a, s);
   if (vt == PFEM_F64 && ct == PFEM_F32) return dispatch_kind<double, float>(P, ops, a, s);
   if (vt == PFEM_F64 && ct == PFEM_F64) return dispatch_kind<double, double>(P, ops, a, s);

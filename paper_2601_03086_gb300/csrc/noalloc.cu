@@ -57,8 +57,8 @@ extern "C" pfem_status pfem_tangent_apply_noalloc(pfem_mesh_t m, pfem_dtype dt, 
     set_error("null mesh");
     return PFEM_ERR_INVALID_ARG;
   }
-  if (m->n_spring_nodes) {
-    set_error("pfem_tangent_apply_noalloc does not include penalty springs");
+  if (m->n_spring_nodes || m->plan.elem_npe) {
+    set_error("pfem_tangent_apply_noalloc: simplex meshes without penalty springs only");
     return PFEM_ERR_UNSUPPORTED;
   }
   if (dt != PFEM_F32 && dt != PFEM_F64 && dt != PFEM_F64_F32) {

@@ -160,7 +160,23 @@ struct DevPlan {
   const float* f_ext_f;  // n_dofs, the same rounded to FP32
   const double* dvalues; // n_dofs prescribed values at full load
   const uint8_t* dmask;  // n_dofs
+  // quadrilaterals (quad.cu): elem_npe = 4 (Q4) or 8 (Q8), 0 for simplex meshes. Element-major
+  // path: one thread per element over its Gauss points writes one record per (element, local
+  // node) to qbuf; each node sums its records in ascending (element, local) order (CSR).
+  // n_tiles counts blocks of kQuadBlock elements (energy and p.Ap partials per block).
+  int elem_npe;
+  int64_t n_elems;
+  const int32_t* qconn;  // n_elems x npe
+  const double2* qxd;    // node coordinates
+  const float2* qxf;
+  const double2* qmatd;  // per element (mu, lambda)
+  const float2* qmatf;
+  const int32_t* qptr;   // n_nodes + 1
+  const int32_t* qidx;   // element * npe + local, ascending per node
+  void* qbuf;            // kMaxRegions x n_elems x npe x 2 values (double capacity)
 };
+
+constexpr int kQuadBlock = 128;  // elements per block of the quadrilateral element kernel
 
 // Operation bits of the element-tile kernel.
 enum : int {
@@ -316,9 +332,12 @@ inline int serve_update_blocks(int64_t n) {
   return (int)(b < 1 ? 1 : (b > 296 ? 296 : b));
 }
 
-// Launches the tile kernel and the halo pass for one mesh (kernels_tile.cu).
+// Launches the tile kernel and the halo pass for one mesh (kernels_tile.cu); quadrilateral
+// meshes go to launch_quad_op.
 pfem_status launch_element_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dtype ct,
                               const OpArgs& a, cudaStream_t s);
+// Element operators of quadrilateral meshes (quad.cu); same contract as launch_element_op.
+pfem_status launch_quad_op(const DevPlan& P, int ops, pfem_dtype vt, pfem_dtype ct, const OpArgs& a, cudaStream_t s);
 
 // Launches the persistent PCG kernel (FP32 element arithmetic only); PFEM_ERR_UNSUPPORTED
 // when it cannot run here (other arithmetic, no co-resident grid), without side effects.

@@ -288,8 +288,8 @@ extern "C" pfem_status pfem_solve_linear_multi(pfem_mesh_t m, pfem_dtype dt, int
                                                pfem_solve_info* infos) {
   pfem_status st = check_mesh(m);
   if (st) return st;
-  if (m->plan.kind != PFEM_LINEAR) {
-    set_error("pfem_solve_linear_multi needs a linear-elastic mesh");
+  if (m->plan.kind != PFEM_LINEAR || m->plan.elem_npe) {
+    set_error("pfem_solve_linear_multi needs a linear-elastic simplex mesh");
     return PFEM_ERR_INVALID_ARG;
   }
   if (k < 1 || !b || !u_out || !(tol > 0.0) || max_iter < 0 || (dt != PFEM_F32 && dt != PFEM_F64)) {

@@ -1,0 +1,85 @@
+"""Quadrilateral (Q4 / Q8) element operators and solvers on the GPU against the FP64 oracle
+(oracle/quad.py), through the C ABI.
+
+Bars: residual, tangent action, Jacobi diagonal and energy at FP32 rel L2 <= 1e-5 and FP64
+<= 1e-12 on distorted meshes with prescribed DOFs and edge tractions; linear solves within
+1e-6 of the oracle with iteration counts in the FP32 bar; Newton on the Neo-Hookean beam
+(Q4) and Cook membrane (Q8) within 1e-6 of the oracle's solution and +-2 of its Newton
+count; a warm start near the solution needs fewer Newton steps.
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import pfem_inputs as pi
+from oracle import quad
+from tests.gpu_util import dev, host, pfem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+CORNERS = [(0.0, 0.0), (2.0, 0.3), (2.3, 1.7), (-0.2, 1.2)]
+TOL = {torch.float32: 1e-5, torch.float64: 1e-12}
+
+
+@pytest.mark.parametrize("npe", [4, 8])
+@pytest.mark.parametrize("kind", ["linear", "neohookean"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64], ids=["f32", "f64"])
+def test_quad_operator_matches_oracle(npe, kind, dtype):
+    P = pfem()
+    mats = (1.3, 0.3) if kind == "linear" else (1.0, 4.0)
+    p = pi.quad_problem(9, 7, CORNERS, npe, kind, *mats, traction=(0.2, -0.1), jitter=0.2, seed=npe)
+    m = quad.QuadMesh(p)
+    mesh = P.Mesh(p)
+    rng = np.random.default_rng(7)
+    u = 0.02 * rng.standard_normal(m.n_dofs)
+    v = rng.standard_normal(m.n_dofs)
+    if dtype == torch.float32:
+        u, v = u.astype(np.float32).astype(np.float64), v.astype(np.float32).astype(np.float64)
+    tol = TOL[dtype]
+    r = host(P.pfem_residual(mesh, dev(u, dtype)))
+    assert rel_l2(r, quad.residual(m, u)) <= tol
+    y = host(P.pfem_tangent_apply(mesh, dev(u, dtype), dev(v, dtype)))
+    assert rel_l2(y, quad.tangent_apply(m, u, v)) <= tol
+    d = host(P.pfem_jacobi_diag(mesh, dev(u, dtype), dtype=dtype))
+    free = ~m.mask
+    d_ref = np.where(free, quad.stiffness(m, u).diagonal(), 1.0)
+    assert rel_l2(d, d_ref) <= tol
+    e, es = P.pfem_energy(mesh, dev(u, dtype))
+    es_ref = quad.strain_energy(m, u)
+    assert abs(es - es_ref) <= 10 * tol * abs(es_ref)
+    assert abs(e - (es_ref - quad.external_force(m) @ u)) <= 10 * tol * (abs(es_ref) + abs(quad.external_force(m) @ u))
+    mesh.close()
+
+
+@pytest.mark.parametrize("npe", [4, 8])
+def test_quad_linear_solve_matches_oracle(npe):
+    P = pfem()
+    p = pi.quad_problem(24, 12, [(0, 0), (4, 0), (4, 1), (0, 1)], npe, "linear", 1.0, 0.3, traction=(0.0, -0.01))
+    m = quad.QuadMesh(p)
+    u_ref, it_ref = quad.solve_linear(m, tol=1e-8)
+    mesh = P.Mesh(p)
+    for precision in ("f32", "f64"):
+        u, info = P.pfem_solve_linear(mesh, tol=1e-8, precision=precision)
+        assert rel_l2(host(u), u_ref) <= 1e-6
+        bar = 2 if precision == "f64" else max(2, int(0.015 * it_ref))
+        assert abs(info["iterations"] - it_ref) <= bar, (precision, info, it_ref)
+    mesh.close()
+
+
+@pytest.mark.parametrize("case", ["beam_q4", "cook_q8"])
+def test_quad_newton_matches_oracle_and_warm_start(case):
+    P = pfem()
+    p = pi.nh_beam(50, 50, 4) if case == "beam_q4" else pi.cook_membrane(30, 8)
+    m = quad.QuadMesh(p)
+    u_ref, n_ref = quad.solve_newton(m, tol=1e-8, n_load_steps=2)
+    mesh = P.Mesh(p)
+    u, info = P.pfem_solve_newton(mesh, tol=1e-8, n_load_steps=2)
+    assert info["status"] == 0
+    assert abs(info["newton_iterations"] - n_ref) <= 2, (info, n_ref)
+    assert rel_l2(host(u), u_ref) <= 1e-6
+    warm = pi.make_warm_start(p, u_ref, seed=31)
+    uw, iw = P.pfem_solve_newton(mesh, dev(warm), tol=1e-8, n_load_steps=1)
+    assert iw["newton_iterations"] < info["newton_iterations"]
+    assert rel_l2(host(uw), u_ref) <= 1e-6
+    mesh.close()
