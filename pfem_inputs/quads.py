@@ -73,9 +73,11 @@ def quad_problem(nx, ny, corners, npe, kind, mat_a, mat_b, clamp_side="left", tr
                 name=f"quad{npe}_{nx}x{ny}", seed=seed, npe=npe)
 
 
-def nh_beam(nx=50, ny=50, npe=4, traction=(0.0, -0.05)):
+def nh_beam(nx=50, ny=50, npe=4, traction=(0.0, -0.01)):
     """Neo-Hookean 4 x 1 cantilever (the beam of the hyperelasticity results): mu = 1,
-    lambda = 4, left end clamped, downward traction on the right end."""
+    lambda = 4, left end clamped, downward traction on the right end (the default load bends
+    the tip by about a fifth of the length; the oracle's Newton needs 5 steps from zero in one
+    load step, close to the paper's ~4.9)."""
     return quad_problem(nx, ny, [(0, 0), (4, 0), (4, 1), (0, 1)], npe, "neohookean", 1.0, 4.0, traction=traction)
 
 
