@@ -263,12 +263,18 @@ def main():
     ap.add_argument("--op", choices=["tangent", "residual"], default="tangent", help="probe apply: operator")
     ap.add_argument("--max-iter", type=int, default=100000, help="probe solve: PCG iteration cap")
     ap.add_argument("--k", type=int, default=0, help="probe apply: k > 0 applies to k vectors at once")
+    ap.add_argument("--serving", default=None, metavar="N,HI,EVERY",
+                    help="run only the serving workload on N requests of up to HI tets with the plain loop "
+                         "on every EVERY-th request (config 5: 1000,2000000,10), arrivals at 2x and 0.5x the "
+                         "plain-loop rate; prints one JSON line")
     args = ap.parse_args()
     if args.oracle_worker is not None:
         print(json.dumps(cpu_oracle_warm_solve(tuple(args.oracle_worker))))
         return 0
     if args.probe is not None:
         return probe(args)
+    if args.serving is not None:
+        return serving_only(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -612,21 +618,26 @@ def _batch_loss(P, pi, torch, np, peak=None):
             "fp32_vs_fp64_rel_l2": {"gradient": err_g, "hvp": err_h}}
 
 
-def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
-    """Scaled sample of the serving workload: the first n_req records of the seeded request
-    stream (Poisson arrivals, 70% linear cubes / 30% Neo-Hookean bars at 10% stretch, 50%
-    warm started), mesh sizes log-uniform in [2k, hi] tets (the full stream goes to 2M), tol
-    1e-8; zero-start Neo-Hookean requests take 5 load steps, warm-started ones 1. The
-    arrival rate is rate_factor x the measured plain-loop solves/s (saturating: the served
-    solves/s is the server's capacity, not the arrival rate).
-    Served: every request submitted at its arrival time to one server (120 GB admission
-    budget), completions polled; solves/s = requests / makespan, latency = completion -
-    arrival. Plain loop: the same requests one at a time, each creating its mesh and solving
-    with the host-synchronised one-iteration-at-a-time loop. Warm starts are an FP64 solve
-    to 1e-12 on this GPU plus the seeded smooth 1% perturbation (input preparation, untimed)."""
+def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain_every=1, ref_tol=1e-12,
+             ref_precision="f64", budget=120 << 30, timeout_s=900.0):
+    """The serving workload: the first n_req records of the seeded request stream (Poisson
+    arrivals, 70% linear cubes / 30% Neo-Hookean bars at 10% stretch, 50% warm started), mesh
+    sizes log-uniform in [2k, hi] tets (config 5 is 1,000 requests up to 2M), tol 1e-8;
+    zero-start Neo-Hookean requests take 5 load steps, warm-started ones 1.
+    Plain loop (and graph loop): the requests one at a time, each creating its mesh (host
+    planning + upload, timed separately) and solving with the host-synchronised
+    one-iteration-at-a-time loop (graph loop: the device while-loop); with plain_every = k only
+    every k-th request runs and the loop's time is that sample's sum times k (an unbiased
+    estimate: the loop's time is the sum of independent per-request times).
+    Served: every request submitted at its arrival time to one server (`budget` bytes of
+    admission budget), arrivals at rate_factor x the plain loop's solves/s for each factor
+    (2 = saturating, 0.5 = latency run); solves/s = requests / makespan, latency = completion
+    - arrival. Warm starts perturb a solve of the request to ref_tol (input preparation,
+    untimed); the served solutions are compared with those references (FP32-vs-FP64 line)."""
     reqs = pi.cfg5_requests(n_requests=n_req, seed=5, hi=hi)
     probs = [pi.request_problem(r) for r in reqs]
     u0s, urefs = [], []
+    t_prep = time.perf_counter()
     for r, p in zip(reqs, probs):
         urefs.append(None)
         if not r["warm"]:
@@ -634,18 +645,20 @@ def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
             continue
         m = P.Mesh(p)
         if r["kind"] == "linear":
-            u, info = P.pfem_solve_linear(m, tol=1e-12, precision="f64", raise_on_error=False)
+            u, info = P.pfem_solve_linear(m, tol=ref_tol, precision=ref_precision, raise_on_error=False)
         else:
             for ls in (5, 20):
-                u, info = P.pfem_solve_newton(m, tol=1e-12, n_load_steps=ls, precision="f64", raise_on_error=False)
+                u, info = P.pfem_solve_newton(m, tol=ref_tol, n_load_steps=ls, precision=ref_precision,
+                                              raise_on_error=False)
                 if info["status"] == 0:
                     break
         m.close()
         if info["status"] != 0:  # no reference solution to perturb: served as a zero start
             u0s.append(None)
             continue
-        urefs[-1] = u.cpu().numpy()  # FP64-operator solution to 1e-12
+        urefs[-1] = u.cpu().numpy()
         u0s.append(pi.make_warm_start(p, urefs[-1], seed=1 + r["seed"] % 100000))
+    t_prep = time.perf_counter() - t_prep
 
     def steps(r, u0):
         return 1 if (r["kind"] == "linear" or u0 is not None) else 5
@@ -658,15 +671,17 @@ def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
             u, info = P.pfem_solve_newton(m, u0d, tol=TOL, n_load_steps=steps(r, u0), raise_on_error=False)
         return u.cpu(), info
 
-    out = {"requests": n_req, "tets_range": [2000, hi],
-           "tets_total": int(sum(r["n_tets"] for r in reqs)),
-           "linear": sum(r["kind"] == "linear" for r in reqs), "warm": sum(u is not None for u in u0s)}
+    sample = list(range(0, n_req, plain_every))
+    out = {"requests": n_req, "tets_range": [2000, hi], "budget_bytes": budget,
+           "tets_total": int(sum(r["n_tets"] for r in reqs)), "warm_start_prep_s": t_prep,
+           "linear": sum(r["kind"] == "linear" for r in reqs), "warm": sum(u is not None for u in u0s),
+           "plain_loop_sample": {"every": plain_every, "requests": len(sample)}}
     for mode_name, mode in (("plain_loop", MODES["plain"]), ("graph_loop", MODES["graph"])):
         P.pfem_set_solver_mode(mode)
         torch.cuda.synchronize()
-        lat, ok, plan_s = [], 0, 0.0
-        t0 = time.perf_counter()
-        for r, p, u0 in zip(reqs, probs, u0s):
+        lat, ok, plan_s, total = [], 0, 0.0, 0.0
+        for k in sample:
+            r, p, u0 = reqs[k], probs[k], u0s[k]
             a = time.perf_counter()
             m = P.Mesh(p)  # host planning + upload (the server does this on planner threads)
             b = time.perf_counter()
@@ -674,48 +689,56 @@ def _serving(P, pi, torch, np, n_req=400, rate_factor=20.0, hi=50_000):
             m.close()
             lat.append(time.perf_counter() - a)
             plan_s += b - a
+            total += time.perf_counter() - a
             ok += info["status"] == 0
-        wall = time.perf_counter() - t0
-        out[mode_name] = {"solves_per_s": n_req / wall, "wall_s": wall, "converged": ok,
-                          "plan_upload_s": plan_s, "solves_per_s_excluding_planning": n_req / (wall - plan_s),
+        wall = total * plain_every  # the loop's time for all n_req requests (estimate if sampled)
+        plan_all = plan_s * plain_every
+        out[mode_name] = {"solves_per_s": n_req / wall, "wall_s": wall, "converged_in_sample": ok,
+                          "plan_upload_s": plan_all, "solves_per_s_excluding_planning": n_req / (wall - plan_all),
                           "solve_ms_p50": 1e3 * _pct(lat, 0.5), "solve_ms_p99": 1e3 * _pct(lat, 0.99)}
     P.pfem_set_solver_mode(MODES["graph"])
 
-    rate = rate_factor * out["plain_loop"]["solves_per_s"]
-    out["arrival_rate_per_s"] = rate
-    arrive = np.cumsum([r["gap"] for r in reqs]) / rate
-    server = P.Server(120 << 30, max_slots=128)
-    tickets, t_sub, done = [], [], {}
-    t0 = time.perf_counter()
-    i = 0
-    while len(done) < n_req:
-        now = time.perf_counter() - t0
-        while i < n_req and arrive[i] <= now:
-            r = reqs[i]
-            tickets.append(server.submit(probs[i], u0s[i], TOL, r["kind"] if r["kind"] == "linear" else "newton",
-                                         steps(r, u0s[i])))
-            t_sub.append(time.perf_counter() - t0)
-            i += 1
-        for k, t in enumerate(tickets):
-            if k not in done:
-                res = server.poll(t)
-                if res is not None:
-                    done[k] = (time.perf_counter() - t0, res[0], res[2], res[1])
-        if time.perf_counter() - t0 > 900.0:
-            raise RuntimeError("served requests did not finish in 900 s")
-        time.sleep(0.0005)
-    makespan = max(v[0] for v in done.values()) - arrive[0]
-    server.close()
-    lat = [done[k][0] - t_sub[k] for k in range(n_req)]
-    out["served"] = {"solves_per_s": n_req / makespan, "makespan_s": makespan,
-                     "converged": sum(done[k][1] == 0 for k in range(n_req)),
-                     "latency_ms_p50": 1e3 * _pct(lat, 0.5), "latency_ms_p99": 1e3 * _pct(lat, 0.99),
-                     "pcg_iterations_total": int(sum(done[k][2]["iterations"] for k in range(n_req)))}
-    errs = [float(np.linalg.norm(done[k][3] - urefs[k]) / np.linalg.norm(urefs[k]))
-            for k in range(n_req) if urefs[k] is not None and done[k][1] == 0]
-    out["served"]["fp32_vs_fp64_rel_l2"] = {"requests": len(errs), "max": max(errs) if errs else None,
-                                            "median": _pct(errs, 0.5) if errs else None,
-                                            "reference": "FP64-operator solve to 1e-12 of each warm request"}
+    def served_run(rate_factor):
+        rate = rate_factor * out["plain_loop"]["solves_per_s"]
+        arrive = np.cumsum([r["gap"] for r in reqs]) / rate
+        server = P.Server(budget, max_slots=128)
+        tickets, t_sub, done = [], [], {}
+        t0 = time.perf_counter()
+        i = 0
+        while len(done) < n_req:
+            now = time.perf_counter() - t0
+            while i < n_req and arrive[i] <= now:
+                r = reqs[i]
+                tickets.append(server.submit(probs[i], u0s[i], TOL, r["kind"] if r["kind"] == "linear" else "newton",
+                                             steps(r, u0s[i])))
+                t_sub.append(time.perf_counter() - t0)
+                i += 1
+            for k, t in enumerate(tickets):
+                if k not in done:
+                    res = server.poll(t)
+                    if res is not None:
+                        done[k] = (time.perf_counter() - t0, res[0], res[2], res[1])
+            if time.perf_counter() - t0 > timeout_s:
+                raise RuntimeError("served requests did not finish in %.0f s" % timeout_s)
+            time.sleep(0.0005)
+        makespan = max(v[0] for v in done.values()) - arrive[0]
+        server.close()
+        lat = [done[k][0] - t_sub[k] for k in range(n_req)]
+        errs = [float(np.linalg.norm(done[k][3] - urefs[k]) / np.linalg.norm(urefs[k]))
+                for k in range(n_req) if urefs[k] is not None and done[k][1] == 0]
+        return {"rate_factor": rate_factor, "arrival_rate_per_s": rate, "solves_per_s": n_req / makespan,
+                "makespan_s": makespan, "converged": sum(done[k][1] == 0 for k in range(n_req)),
+                "latency_ms_p50": 1e3 * _pct(lat, 0.5), "latency_ms_p99": 1e3 * _pct(lat, 0.99),
+                "pcg_iterations_total": int(sum(done[k][2]["iterations"] for k in range(n_req))),
+                "vs_reference_rel_l2": {"requests": len(errs), "max": max(errs) if errs else None,
+                                        "median": _pct(errs, 0.5) if errs else None,
+                                        "reference": "%s solve of each warm request to %g" % (ref_precision, ref_tol)}}
+
+    runs = [served_run(f) for f in rate_factors]
+    out["served"] = runs[0]
+    if len(runs) > 1:
+        out["served_runs"] = runs
+    out["served"]["fp32_vs_fp64_rel_l2"] = runs[0]["vs_reference_rel_l2"]
     out["speedup_vs_plain_loop"] = out["served"]["solves_per_s"] / out["plain_loop"]["solves_per_s"]
     out["speedup_vs_plain_loop_excluding_planning"] = (out["served"]["solves_per_s"] /
                                                        out["plain_loop"]["solves_per_s_excluding_planning"])
@@ -822,6 +845,25 @@ def probe(a):
                     "us_per_iteration": 1e3 * ms / max(info["iterations"], 1)})
     print(json.dumps(out))
     mesh.close()
+    return 0
+
+
+def serving_only(a):
+    """The serving measurement alone (config 5 at full size takes tens of minutes)."""
+    import numpy as np
+    import torch
+
+    import pfem_inputs as pi
+    import paper_2601_03086_gb300 as P
+    from paper_2601_03086_gb300 import build
+
+    build.build()
+    n, hi, every = (int(x) for x in a.serving.split(","))
+    out = _serving(P, pi, torch, np, n_req=n, rate_factors=(2.0, 0.5), hi=hi, plain_every=every, ref_tol=1e-10,
+                   ref_precision="f32", timeout_s=3600.0)
+    out["workload"] = "config 5 serving stream: %d requests, %d..%d tets, arrivals at 2x and 0.5x the plain rate" % (
+        n, 2000, hi)
+    print(json.dumps(out))
     return 0
 
 
