@@ -60,20 +60,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) multi_kernel(DevPlan P, Multi
     const int ja = M.j0 + 2 * pr, jb = ja + 1;  // the pair's vectors (jb may be past k)
     const bool has_b = jb < M.k;
     __syncthreads();  // the previous pair's node pass has read its slots
-    // ---- the pair's field on the tile's nodes (0 on prescribed DOFs), relative to its value
-    // at the tile's first node (differences in FP64 before rounding; see process_tile)
-    auto field = [&](int j, int64_t k, bool fixed) { return fixed ? 0.0 : (double)v[(int64_t)j * nd + k]; };
-    double aa[3] = {0.0, 0.0, 0.0}, ab[3] = {0.0, 0.0, 0.0};
-    if (nl > 0) {
-      const unsigned info0 = (unsigned)sinfo[0];
-      const int64_t gid0 = (int64_t)(info0 & kInfoIdMask);
-#pragma unroll
-      for (int i = 0; i < DIM; ++i) {
-        const bool f0 = ((info0 >> kInfoIdBits) >> i) & 1u;
-        aa[i] = field(ja, gid0 * DIM + i, f0);
-        ab[i] = has_b ? field(jb, gid0 * DIM + i, f0) : 0.0;
-      }
-    }
+    // ---- the pair's field on the tile's nodes (0 on prescribed DOFs)
     for (int l = threadIdx.x; l < nl; l += blockDim.x) {
       const unsigned info = (unsigned)sinfo[l];
       const int64_t gid = (int64_t)(info & kInfoIdMask);
@@ -83,8 +70,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) multi_kernel(DevPlan P, Multi
       for (int i = 0; i < DIM; ++i) {
         const int64_t k = gid * DIM + i;
         const bool fixed = (mask >> i) & 1u;
-        w[i].x = (float)(field(ja, k, fixed) - aa[i]);
-        w[i].y = has_b ? (float)(field(jb, k, fixed) - ab[i]) : 0.f;
+        w[i].x = fixed ? 0.f : (float)v[(int64_t)ja * nd + k];
+        w[i].y = (fixed || !has_b) ? 0.f : (float)v[(int64_t)jb * nd + k];
       }
       st_pair(smem + L.v, l, w, DIM);
     }

@@ -295,21 +295,6 @@ __global__ void __launch_bounds__(kTileThreads, KIND == K_LIN ? 4 : 3)
       const double beta = s_beta;
       const double* p_old = odd ? sA.p[1] : sA.p[0];
       double* p_new = odd ? sA.p[0] : sA.p[1];
-      auto dir = [&](int64_t k, bool fixed) {  // the formula of pcg_direction
-        return fixed ? 0.0 : fma(sA.dinv[k], __ldcg(sA.r + k), beta * __ldcg(p_old + k));
-      };
-      double va[3] = {0.0, 0.0, 0.0};  // anchor: the tile's first node (as process_tile)
-      if (s_nl > 0) {
-        const unsigned info0 = (unsigned)sinfo[0];
-        const int64_t gid0 = (int64_t)(info0 & kInfoIdMask);
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) va[i] = dir(gid0 * DIM + i, ((info0 >> kInfoIdBits) >> i) & 1u);
-        if (threadIdx.x == 0) {
-          float* sa = reinterpret_cast<float*>(smem + L.red) + 16;
-#pragma unroll
-          for (int i = 0; i < 3; ++i) sa[i] = (float)va[i];
-        }
-      }
       for (int l = threadIdx.x, nl = s_nl, ncomp = s_ncomp; l < nl; l += blockDim.x) {
         const unsigned info = (unsigned)sinfo[l];
         const int64_t gid = (int64_t)(info & kInfoIdMask);
@@ -318,9 +303,10 @@ __global__ void __launch_bounds__(kTileThreads, KIND == K_LIN ? 4 : 3)
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
           const int64_t k = gid * DIM + i;
-          const double pn = dir(k, (mask >> i) & 1u);
+          const bool fixed = (mask >> i) & 1u;
+          const double pn = fixed ? 0.0 : fma(sA.dinv[k], __ldcg(sA.r + k), beta * __ldcg(p_old + k));
           if (l < ncomp) p_new[k] = pn;  // complete nodes: this tile owns the DOF
-          w[i] = (float)(pn - va[i]);
+          w[i] = (float)pn;
         }
         st4(sv + 4 * l, w[0], w[1], w[2], 0.f);
       }
@@ -348,7 +334,7 @@ __global__ void __launch_bounds__(kTileThreads, KIND == K_LIN ? 4 : 3)
 #pragma unroll
           for (int i = 0; i < DIM; ++i) acc[i] += tt[i];
         }
-        e_acc += pap_node<DIM, float>(sv + 4 * l, reinterpret_cast<const float*>(smem + L.red) + 16, acc);
+        e_acc += pap_node<DIM, float>(sv + 4 * l, acc);  // as node_pass
         if (l < ncomp) {
           const unsigned info = (unsigned)sinfo[l];
           const int64_t gid = (int64_t)(info & kInfoIdMask);

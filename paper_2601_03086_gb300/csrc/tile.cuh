@@ -342,12 +342,11 @@ __device__ __forceinline__ void fan_pass(unsigned char* smem, const SmemLayout<C
 // p_l . (A_tile p)_l of one tile node in the element precision (summed in FP64 over the tile's
 // nodes this is the tile's share of p . A p: every element contribution to node l sits in
 // one of l's slots)
-// v: the node's staged field, a: the tile's anchor value (the field is v + a).
 template <int DIM, typename CT>
-__device__ __forceinline__ double pap_node(const CT* v, const CT* a, const CT (&acc)[4]) {
-  CT d = (v[0] + a[0]) * acc[0];
+__device__ __forceinline__ double pap_node(const CT* v, const CT (&acc)[4]) {
+  CT d = v[0] * acc[0];
 #pragma unroll
-  for (int i = 1; i < DIM; ++i) d = fma(v[i] + a[i], acc[i], d);
+  for (int i = 1; i < DIM; ++i) d = fma(v[i], acc[i], d);
   return (double)d;
 }
 
@@ -374,9 +373,7 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
 #pragma unroll
       for (int i = 0; i < DIM; ++i) acc[i] += t[i];
     }
-    if constexpr (PCG)
-      *e_pap += pap_node<DIM, CT>(reinterpret_cast<const CT*>(smem + L.v) + 4 * l,
-                                  reinterpret_cast<const CT*>(smem + L.red) + 16, acc);
+    if constexpr (PCG) *e_pap += pap_node<DIM, CT>(reinterpret_cast<const CT*>(smem + L.v) + 4 * l, acc);
     if (l < ncomp) {
       const unsigned info = (unsigned)sinfo[l];
       final_write<DIM, OUT, VT, CT, PCG>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, acc, sc);
@@ -517,32 +514,6 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
     }
     // nodes, two per thread and round: records (the first round's are in flight already),
     // then the gathers their ids select
-    // Fields are staged relative to their value at the tile's first node (the anchor), the
-    // difference taken in FP64 before rounding to the element precision: the element
-    // arithmetic only uses differences between nodes (constants are in the null space of
-    // the operator), so FP32 keeps its relative accuracy on smooth fields of large magnitude.
-    double ua[3] = {0.0, 0.0, 0.0}, va[3] = {0.0, 0.0, 0.0};
-    if (nl > 0) {
-      const unsigned info0 = (unsigned)__float_as_int(P.lnode_f[lbeg].w);
-      const int64_t gid0 = (int64_t)(info0 & kInfoIdMask);
-      const unsigned mask0 = info0 >> kInfoIdBits;
-      if constexpr (NEED_U) {
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) ua[i] = (double)u[gid0 * DIM + i];
-      }
-      if constexpr (PCG) {
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) va[i] = pcg_direction(A.pcg, p_old, beta, gid0 * DIM + i, (mask0 >> i) & 1u);
-      } else if constexpr (NEED_V) {
-#pragma unroll
-        for (int i = 0; i < DIM; ++i) va[i] = ((mask0 >> i) & 1u) ? 0.0 : (double)v[gid0 * DIM + i];
-      }
-      if (threadIdx.x == 0) {  // the node pass of the PCG-fused apply adds it back for p . A p
-        CT* sa = reinterpret_cast<CT*>(smem + L.red) + 16;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) sa[i] = CT(va[i]);
-      }
-    }
     for (int l0 = threadIdx.x; l0 < nl; l0 += 2 * blockDim.x) {
       const int ls[2] = {l0, l0 + (int)blockDim.x};
       if (l0 != (int)threadIdx.x) load_records(l0);
@@ -557,7 +528,7 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
         const unsigned mask = info >> kInfoIdBits;
         if constexpr (NEED_U) {
 #pragma unroll
-          for (int i = 0; i < DIM; ++i) wu[q][i] = CT((double)u[gid * DIM + i] - ua[i]);
+          for (int i = 0; i < DIM; ++i) wu[q][i] = CT(u[gid * DIM + i]);
         }
         if constexpr (PCG) {
 #pragma unroll
@@ -565,12 +536,11 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
             const int64_t k = gid * DIM + i;
             const double pn = pcg_direction(A.pcg, p_old, beta, k, (mask >> i) & 1u);
             if (ls[q] < ncomp) p_new[k] = pn;  // complete nodes: this tile owns the DOF
-            wv[q][i] = CT(pn - va[i]);
+            wv[q][i] = CT(pn);
           }
         } else if constexpr (NEED_V) {
 #pragma unroll
-          for (int i = 0; i < DIM; ++i)
-            wv[q][i] = CT((((mask >> i) & 1u) ? 0.0 : (double)v[gid * DIM + i]) - va[i]);
+          for (int i = 0; i < DIM; ++i) wv[q][i] = ((mask >> i) & 1u) ? CT(0) : CT(v[gid * DIM + i]);
         }
       }
 #pragma unroll
