@@ -61,17 +61,6 @@ template <>
 __device__ __forceinline__ const double* qmat_ptr<double>(const DevPlan& P) {
   return reinterpret_cast<const double*>(P.qmatd);
 }
-template <typename CT>
-__device__ __forceinline__ const CT* qx_ptr(const DevPlan& P);
-template <>
-__device__ __forceinline__ const float* qx_ptr<float>(const DevPlan& P) {
-  return reinterpret_cast<const float*>(P.qxf);
-}
-template <>
-__device__ __forceinline__ const double* qx_ptr<double>(const DevPlan& P) {
-  return reinterpret_cast<const double*>(P.qxd);
-}
-
 // Sum over the block's threads (warps in index order), valid in thread 0.
 __device__ __forceinline__ double qblock_sum(double v, double* red) {
 #pragma unroll
@@ -104,8 +93,23 @@ __global__ void __launch_bounds__(kQuadBlock) quad_elem_kernel(DevPlan P, OpArgs
   int inv = 0;
   double e_acc = 0.0;
   if (live) {
-    const CT* X = qx_ptr<CT>(P);
+    // element-relative coordinates formed in FP64 (sum_a dN_a = 0 leaves J unchanged), so
+    // that FP32 geometry keeps its relative accuracy far from the origin
+    const double* X = reinterpret_cast<const double*>(P.qxd);
     const CT* M = qmat_ptr<CT>(P);
+    const int64_t n0 = P.qconn[e * NPE];
+    const double x00 = X[2 * n0], x01 = X[2 * n0 + 1];
+    // fields likewise relative to node 0 (the element arithmetic only uses their gradients)
+    const VT* usrc = static_cast<const VT*>(A.u);
+    auto fld = [&](const VT* f, int64_t n, int i, bool masked) {
+      return (masked && P.dmask[2 * n + i]) ? 0.0 : (double)f[2 * n + i];
+    };
+    double ua[2] = {0.0, 0.0}, va[2] = {0.0, 0.0};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      if (NEED_U) ua[i] = fld(usrc, n0, i, false);
+      if (NEED_V) va[i] = fld(vsrc, n0, i, true);
+    }
     mu = M[2 * e];
     lam = M[2 * e + 1];
 #pragma unroll
@@ -113,9 +117,9 @@ __global__ void __launch_bounds__(kQuadBlock) quad_elem_kernel(DevPlan P, OpArgs
       const int64_t n = P.qconn[e * NPE + a];
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
-        x[a][i] = X[2 * n + i];
-        u[a][i] = NEED_U ? CT(static_cast<const VT*>(A.u)[2 * n + i]) : CT(0);
-        v[a][i] = NEED_V ? (P.dmask[2 * n + i] ? CT(0) : CT(vsrc[2 * n + i])) : CT(0);
+        x[a][i] = CT(X[2 * n + i] - (i == 0 ? x00 : x01));
+        u[a][i] = NEED_U ? CT(fld(usrc, n, i, false) - ua[i]) : CT(0);
+        v[a][i] = NEED_V ? CT(fld(vsrc, n, i, true) - va[i]) : CT(0);
         acc[a][i] = CT(0);
       }
     }
@@ -239,10 +243,11 @@ __global__ void __launch_bounds__(kQuadBlock) quad_elem_kernel(DevPlan P, OpArgs
         buf[2 * a + 1] = acc[a][1];
       }
     }
-    if constexpr (PCG) {
+    if constexpr (PCG) {  // p_e . (A_e p_e) with the anchor added back
       CT d = CT(0);
 #pragma unroll
-      for (int a = 0; a < NPE; ++a) d = fma(v[a][0], acc[a][0], fma(v[a][1], acc[a][1], d));
+      for (int a = 0; a < NPE; ++a)
+        d = fma(v[a][0] + CT(va[0]), acc[a][0], fma(v[a][1] + CT(va[1]), acc[a][1], d));
       e_acc = (double)d;
     }
   }

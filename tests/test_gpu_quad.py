@@ -37,7 +37,7 @@ def test_quad_operator_matches_oracle(npe, kind, dtype):
     m = quad.QuadMesh(p)
     mesh = P.Mesh(p)
     rng = np.random.default_rng(7)
-    u = 0.02 * rng.standard_normal(m.n_dofs)
+    u = 0.004 * rng.standard_normal(m.n_dofs)  # small enough that no Gauss point inverts
     v = rng.standard_normal(m.n_dofs)
     if dtype == torch.float32:
         u, v = u.astype(np.float32).astype(np.float64), v.astype(np.float32).astype(np.float64)
