@@ -263,10 +263,11 @@ def main():
     ap.add_argument("--op", choices=["tangent", "residual"], default="tangent", help="probe apply: operator")
     ap.add_argument("--max-iter", type=int, default=100000, help="probe solve: PCG iteration cap")
     ap.add_argument("--k", type=int, default=0, help="probe apply: k > 0 applies to k vectors at once")
-    ap.add_argument("--serving", default=None, metavar="N,HI,EVERY",
+    ap.add_argument("--serving", default=None, metavar="N,HI,EVERY[,NLAT]",
                     help="run only the serving workload on N requests of up to HI tets with the plain loop "
-                         "on every EVERY-th request (config 5: 1000,2000000,10), arrivals at 2x and 0.5x the "
-                         "plain-loop rate; prints one JSON line")
+                         "on every EVERY-th request (config 5: 1000,2000000,20,200): served with all arrivals "
+                         "at t=0 and at 2x the plain-loop rate, and the first NLAT requests at 0.5x; prints "
+                         "one JSON line")
     args = ap.parse_args()
     if args.oracle_worker is not None:
         print(json.dumps(cpu_oracle_warm_solve(tuple(args.oracle_worker))))
@@ -631,7 +632,8 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
     estimate: the loop's time is the sum of independent per-request times).
     Served: every request submitted at its arrival time to one server (`budget` bytes of
     admission budget), arrivals at rate_factor x the plain loop's solves/s for each factor
-    (2 = saturating, 0.5 = latency run); solves/s = requests / makespan, latency = completion
+    (inf = all at t = 0, the server's capacity; 2; 0.5 = latency run), an entry (factor, n)
+    serving only the first n requests; solves/s = requests / makespan, latency = completion
     - arrival. Warm starts perturb a solve of the request to ref_tol (input preparation,
     untimed); the served solutions are compared with those references (FP32-vs-FP64 line)."""
     reqs = pi.cfg5_requests(n_requests=n_req, seed=5, hi=hi)
@@ -698,16 +700,17 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
                           "solve_ms_p50": 1e3 * _pct(lat, 0.5), "solve_ms_p99": 1e3 * _pct(lat, 0.99)}
     P.pfem_set_solver_mode(MODES["graph"])
 
-    def served_run(rate_factor):
+    def served_run(rate_factor, n_run=None):
+        n_run = n_req if n_run is None else min(n_run, n_req)
         rate = rate_factor * out["plain_loop"]["solves_per_s"]
-        arrive = np.cumsum([r["gap"] for r in reqs]) / rate
+        arrive = np.cumsum([r["gap"] for r in reqs[:n_run]]) / rate  # rate_factor inf: all at t = 0
         server = P.Server(budget, max_slots=128)
         tickets, t_sub, done = [], [], {}
         t0 = time.perf_counter()
         i = 0
-        while len(done) < n_req:
+        while len(done) < n_run:
             now = time.perf_counter() - t0
-            while i < n_req and arrive[i] <= now:
+            while i < n_run and arrive[i] <= now:
                 r = reqs[i]
                 tickets.append(server.submit(probs[i], u0s[i], TOL, r["kind"] if r["kind"] == "linear" else "newton",
                                              steps(r, u0s[i])))
@@ -723,18 +726,19 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
             time.sleep(0.0005)
         makespan = max(v[0] for v in done.values()) - arrive[0]
         server.close()
-        lat = [done[k][0] - t_sub[k] for k in range(n_req)]
+        lat = [done[k][0] - t_sub[k] for k in range(n_run)]
         errs = [float(np.linalg.norm(done[k][3] - urefs[k]) / np.linalg.norm(urefs[k]))
-                for k in range(n_req) if urefs[k] is not None and done[k][1] == 0]
-        return {"rate_factor": rate_factor, "arrival_rate_per_s": rate, "solves_per_s": n_req / makespan,
-                "makespan_s": makespan, "converged": sum(done[k][1] == 0 for k in range(n_req)),
+                for k in range(n_run) if urefs[k] is not None and done[k][1] == 0]
+        return {"rate_factor": rate_factor if np.isfinite(rate_factor) else "all at t=0", "requests": n_run,
+                "arrival_rate_per_s": rate if np.isfinite(rate) else None, "solves_per_s": n_run / makespan,
+                "makespan_s": makespan, "converged": sum(done[k][1] == 0 for k in range(n_run)),
                 "latency_ms_p50": 1e3 * _pct(lat, 0.5), "latency_ms_p99": 1e3 * _pct(lat, 0.99),
-                "pcg_iterations_total": int(sum(done[k][2]["iterations"] for k in range(n_req))),
+                "pcg_iterations_total": int(sum(done[k][2]["iterations"] for k in range(n_run))),
                 "vs_reference_rel_l2": {"requests": len(errs), "max": max(errs) if errs else None,
                                         "median": _pct(errs, 0.5) if errs else None,
                                         "reference": "%s solve of each warm request to %g" % (ref_precision, ref_tol)}}
 
-    runs = [served_run(f) for f in rate_factors]
+    runs = [served_run(*(f if isinstance(f, tuple) else (f,))) for f in rate_factors]
     out["served"] = runs[0]
     if len(runs) > 1:
         out["served_runs"] = runs
@@ -858,11 +862,14 @@ def serving_only(a):
     from paper_2601_03086_gb300 import build
 
     build.build()
-    n, hi, every = (int(x) for x in a.serving.split(","))
-    out = _serving(P, pi, torch, np, n_req=n, rate_factors=(2.0, 0.5), hi=hi, plain_every=every, ref_tol=1e-10,
-                   ref_precision="f32", timeout_s=3600.0)
-    out["workload"] = "config 5 serving stream: %d requests, %d..%d tets, arrivals at 2x and 0.5x the plain rate" % (
-        n, 2000, hi)
+    f = [int(x) for x in a.serving.split(",")]
+    n, hi, every = f[:3]
+    n_lat = f[3] if len(f) > 3 else n
+    out = _serving(P, pi, torch, np, n_req=n, rate_factors=((float("inf"), n), (2.0, n), (0.5, n_lat)), hi=hi,
+                   plain_every=every, ref_tol=1e-10, ref_precision="f32", timeout_s=3600.0)
+    out["workload"] = ("serving stream: %d requests, %d..%d tets; served with every request submitted at t=0 "
+                       "(capacity) and at 2x the plain-loop rate, and the first %d requests at 0.5x (latency)"
+                       % (n, 2000, hi, n_lat))
     print(json.dumps(out))
     return 0
 
