@@ -25,6 +25,8 @@ timed on this host.
     --probe solve --n 40 --max-iter 40 [--solver-mode plain]
         Jacobi-PCG solves of the n^3 cube (the benchmark workload at n = 40); plain runs one
         kernel at a time, so that a profiler attributes time per kernel
+    --probe attn --n 1048576 --reps 3
+        physics-attention forwards on n points (128 channels, 128 tokens, 8 heads)
   and prints one JSON line with CUDA-event timings after warm-up.
 
 --impl reference times the FP64 CPU oracle (global sparse assembly + Jacobi-PCG) on the
@@ -254,7 +256,7 @@ def main():
                     help="graph (device while loop, default), persistent (one cooperative launch per "
                          "replacement interval) or plain (one launch per kernel, for profiler launch lists)")
     ap.add_argument("--oracle-worker", nargs=2, type=int, default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--probe", choices=["apply", "solve"], default=None,
+    ap.add_argument("--probe", choices=["apply", "solve", "attn"], default=None,
                     help="run one kernel-level driver (see the module docstring) instead of the benchmark")
     ap.add_argument("--n", type=int, default=40, help="probe: cube of n^3 hexes x 6 tets")
     ap.add_argument("--reps", type=int, default=3, help="probe: timed repetitions after one warm-up")
@@ -463,6 +465,7 @@ def main():
             extras["newton"] = _newton(P, pi, torch, peak)
             extras["batch_loss"] = _batch_loss(P, pi, torch, np, peak)
             extras["serving"] = _serving(P, pi, torch, np)
+            extras["attention"] = _attention(P, torch, np, peak)
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -750,6 +753,69 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
     return out
 
 
+def _attention(P, torch, np, peak, n=1 << 20, S=128, H=8, reps=20):
+    """Physics-attention forward (Method, subsection "Transolver"): C = 128 channels, S = 128
+    tokens, 8 heads, bf16 activations, on the 131,072 material points of a 64^3 gyroid cell
+    (the homogenisation backbone's input) and on 2^20 points (inputs beyond L2: X, M and X^t
+    are 256 MB each), random weights.  CUDA events around each forward on the module's stream
+    and around each of its kernels (timing on).  Algorithmic HBM bytes per point: X 2C,
+    M written and read 2 x 2 S_pad, X^t 2C; tensor flops per point: 2C(C+S) + 2S(C+1) + 2SC."""
+    import pfem_inputs.attention as ai
+
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            tc_peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        tc_peak = 1900.0
+    C, SP = 128, (64 if S <= 64 else 128)
+    params = ai.layer_params(C, S, seed=5, slice_gain=4.0)
+    attn = P.Attention(params, H, 1.0)
+    out = {"channels": C, "tokens": S, "heads": H, "dtype": "bf16 activations, FP32 accumulate",
+           "weights": "random (no trained weights)"}
+
+    def run(x, label):
+        xt = torch.empty_like(x)
+        for _ in range(3):
+            attn.forward(x, xt)
+        a, b = _events(torch)
+        a.record()
+        for _ in range(reps):
+            attn.forward(x, xt)
+        b.record()
+        b.synchronize()
+        attn.sync()
+        ms = a.elapsed_time(b) / reps
+        attn.set_timing(True)
+        attn.forward(x, xt)
+        k = attn.kernel_ms()
+        attn.set_timing(False)
+        npts = x.shape[0]
+        alg = npts * (2 * C + 4 * SP + 2 * C)
+        flops = npts * (2 * C * (C + S) + 2 * S * (C + 1) + 2 * S * C)
+        tot_k = sum(k.values())
+        dom = max(("slice", "deslice"), key=lambda q: k[q])
+        dom_bytes = npts * ((2 * C + 2 * SP) if dom == "slice" else (2 * SP + 2 * C))
+        dom_flops = npts * ((2 * C * (C + S) + 2 * S * (C + 1)) if dom == "slice" else 2 * S * C)
+        return {"workload": label, "points": int(npts), "ms_per_forward": ms, "points_per_s": npts / (ms * 1e-3),
+                "kernel_ms": k, "algorithmic_bytes": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9,
+                "hbm_frac": alg / (ms * 1e-3) / 1e9 / peak, "tensor_tflops": flops / (ms * 1e-3) / 1e12,
+                "tensor_frac": flops / (ms * 1e-3) / 1e12 / tc_peak,
+                "dominant_kernel": {"kernel": "attn_%s_kernel<%d>" % (dom, SP), "ms": k[dom],
+                                    "share_of_kernels": k[dom] / tot_k, "algorithmic_bytes": dom_bytes,
+                                    "achieved_gbs": dom_bytes / (k[dom] * 1e-3) / 1e9,
+                                    "hbm_frac": dom_bytes / (k[dom] * 1e-3) / 1e9 / peak,
+                                    "tensor_frac": dom_flops / (k[dom] * 1e-3) / 1e12 / tc_peak}}
+
+    pts = ai.tpms_points(64)
+    x64 = torch.tensor(ai.point_features(pts, C, seed=3).astype(np.float32), device="cuda").to(torch.bfloat16)
+    out["gyroid64"] = run(x64, "64^3 gyroid cell, %d material points" % pts.shape[0])
+    xl = torch.randn((n, C), device="cuda").to(torch.bfloat16)
+    out["large"] = run(xl, "%d points, N(0,1) features" % n)
+    out["peaks"] = {"hbm_gbs": peak, "bf16_tflops": tc_peak, "kind": "measured burst (kernels timed alone)"}
+    attn.close()
+    return out
+
+
 def _newton(P, pi, torch, peak=None):
     """Neo-Hookean bar (config 3): zero start with 5 load steps, warm start with 1; the warm
     solve again in FP64 element arithmetic (FP32-vs-FP64 solution difference) and once in the
@@ -806,6 +872,23 @@ def probe(a):
     from paper_2601_03086_gb300 import build
 
     build.build()
+    if a.probe == "attn":  # physics attention on a.n points, 128 channels, 128 tokens, 8 heads
+        import pfem_inputs.attention as ai
+
+        attn = P.Attention(ai.layer_params(128, 128, seed=5, slice_gain=4.0), 8, 1.0)
+        x = torch.randn((a.n, 128), device="cuda").to(torch.bfloat16)
+        xt = torch.empty_like(x)
+        attn.forward(x, xt)
+        ev = _events(torch)
+        ev[0].record()
+        for _ in range(a.reps):
+            attn.forward(x, xt)
+        ev[1].record()
+        ev[1].synchronize()
+        attn.sync()
+        print(json.dumps({"probe": "attn", "n": a.n, "forward_us": ev[0].elapsed_time(ev[1]) * 1e3 / a.reps}))
+        attn.close()
+        return 0
     p = pi.cube_problem(a.n, seed=2) if a.kind == "linear" else pi.bar_problem(4 * a.n, a.n, a.n, seed=3)
     mesh = P.Mesh(p)
     out = {"probe": a.probe, "n": a.n, "stats": mesh.stats()}

@@ -381,6 +381,62 @@ pfem_status pfem_serve_drain(pfem_server_t server, double timeout_s);
 /* Stops the server; requests still running are abandoned. */
 void pfem_serve_destroy(pfem_server_t server);
 
+/* ---- physics attention (Sec. "Transolver") ------------------------------------------
+ *
+ * The physics-attention module of the Transolver backbone that produces the warm starts, for
+ * N points with C feature channels X (N x C) and S physics-aware tokens:
+ *   U = X W_U + b_U (N x C);  M = softmax over the S tokens of X W_M + b_M (N x S);
+ *   Z_J = sum_I M_IJ U_I / sum_I M_IJ (S x C; a token whose weight sum is 0 is the zero row);
+ *   Q, K, V = Z W_Q + b_Q, Z W_K + b_K, Z W_V + b_V; per head h (C/H channels each)
+ *   Z^t_h = softmax(scale Q_h K_h^T) V_h (the section prints scale = 1);
+ *   X^t = M Z^t (N x C).
+ * Each "MLP" of the section is one affine map here. Weights are (in, out) matrices.
+ *
+ * Precision: X, X^t and M are bf16 in memory, the projections and sums run on the tensor
+ * cores with FP32 accumulation, U and Z^t are rounded to bf16 before their products; the
+ * tokens, Q/K/V and the attention are FP32. Results are bitwise reproducible. */
+typedef struct pfem_attn_s* pfem_attn_t;
+
+typedef struct {               /* HOST float arrays, read during pfem_attn_create only */
+  const float *wu, *bu;        /* C x C (in, out) and C: the U map; rounded to bf16 */
+  const float *wm, *bm;        /* C x S and S: the slice logits; wm rounded to bf16 */
+  const float *wq, *bq;        /* C x C and C each: the token projections (FP32) */
+  const float *wk, *bk;
+  const float *wv, *bv;
+} pfem_attn_weights;
+
+/* Build a module on the current device with its weights resident. n_channels must be 128;
+ * n_tokens a multiple of 16 in [16, 128]; n_heads divides 128 with at most 64 channels per
+ * head; calls run on cuda_stream (NULL = legacy default stream).
+ * Errors: INVALID_ARG (NULL pointer, non-finite weight or scale), UNSUPPORTED (sizes),
+ * OUT_OF_MEMORY / CUDA. On error *out is NULL. */
+pfem_status pfem_attn_create(int32_t n_channels, int32_t n_tokens, int32_t n_heads, double scale,
+                             const pfem_attn_weights* weights, void* cuda_stream, pfem_attn_t* out);
+
+/* Enqueue the forward pass for n_points points (0 = nothing to do). Device pointers, 16-byte
+ * aligned: x (bf16 [n_points][128], read), xt (bf16 [n_points][128], written), m (bf16
+ * [n_points][S_pad] with S_pad = 64 for S <= 64 and 128 otherwise, written with the slice
+ * weights and zero pad columns; NULL = a workspace of the handle, grown on demand with a
+ * stream synchronisation), z and zt (float [S][128], the tokens Z and Z^t; NULL = not
+ * copied out). Only enqueues work; pfem_attn_sync reports errors raised on the device.
+ * Errors: INVALID_ARG (NULL or misaligned pointer, n_points < 0 or >= 2^31 - 128), CUDA. */
+pfem_status pfem_attn_forward(pfem_attn_t attn, int64_t n_points, const void* x, void* xt, void* m,
+                              float* z, float* zt);
+
+/* Synchronise the module's stream. TIMEOUT if a bounded device wait of an earlier forward
+ * expired (its outputs are then incomplete; the error word is cleared). */
+pfem_status pfem_attn_sync(pfem_attn_t attn);
+
+/* Synchronise the stream and free the module. NULL is ignored. */
+void pfem_attn_destroy(pfem_attn_t attn);
+
+/* Kernel timing of later forwards (on != 0): CUDA events on the module's stream around each
+ * of its four kernels. pfem_attn_kernel_ms waits for the last timed forward and writes the
+ * durations in ms of its slice, token-sum, token-attention and deslice kernels to ms[0..3].
+ * INVALID_ARG when timing is off. */
+pfem_status pfem_attn_set_timing(pfem_attn_t attn, int32_t on);
+pfem_status pfem_attn_kernel_ms(pfem_attn_t attn, double* ms);
+
 /* ---- misc ------------------------------------------------------------------------- */
 
 const char* pfem_last_error(void);

@@ -6,6 +6,11 @@ does, and raises if the library has not been built.
 """
 
 from .api import (  # noqa: F401
+    Attention,
+    pfem_attn_create,
+    pfem_attn_destroy,
+    pfem_attn_forward,
+    pfem_attn_sync,
     Batch,
     Mesh,
     Server,

@@ -84,6 +84,10 @@ class SolveInfo(C.Structure):
     ]
 
 
+class AttnWeights(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("wu", "bu", "wm", "bm", "wq", "bq", "wk", "bk", "wv", "bv")]
+
+
 # name -> (restype, argtypes); every entry must be exported by libpfem.so
 SIGNATURES = {
     "pfem_mesh_create": (C.c_int32, [C.POINTER(MeshDesc), C.c_void_p, C.POINTER(C.c_void_p)]),
@@ -124,6 +128,14 @@ SIGNATURES = {
     "pfem_serve_poll": (C.c_int32, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(SolveInfo)]),
     "pfem_serve_drain": (C.c_int32, [C.c_void_p, C.c_double]),
     "pfem_serve_destroy": (None, [C.c_void_p]),
+    "pfem_attn_create": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.POINTER(AttnWeights), C.c_void_p,
+                                     C.POINTER(C.c_void_p)]),
+    "pfem_attn_forward": (C.c_int32, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                      C.c_void_p]),
+    "pfem_attn_sync": (C.c_int32, [C.c_void_p]),
+    "pfem_attn_destroy": (None, [C.c_void_p]),
+    "pfem_attn_set_timing": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "pfem_attn_kernel_ms": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double)]),
     "pfem_last_error": (C.c_char_p, []),
     "pfem_version": (C.c_char_p, []),
 }

@@ -526,3 +526,89 @@ def pfem_serve_drain(server, timeout_s=600.0):
 
 def pfem_serve_destroy(server):
     server.close()
+
+
+# ---- physics attention ----------------------------------------------------------------
+
+_ATTN_KEYS = ("wu", "bu", "wm", "bm", "wq", "bq", "wk", "bk", "wv", "bv")
+
+
+class Attention:
+    """Owns a pfem_attn_t: the physics-attention module with resident weights.  `params`
+    maps wu, bu, wm, bm, wq, bq, wk, bk, wv, bv to arrays ((in, out) weights); they are
+    copied (as float32) at creation.  Bound to the torch CUDA stream current at creation."""
+
+    def __init__(self, params, n_heads, scale=1.0, stream=None):
+        arrs = {k: np.ascontiguousarray(np.asarray(params[k], dtype=np.float32)) for k in _ATTN_KEYS}
+        self.n_channels = int(arrs["wu"].shape[0])
+        self.n_tokens = int(arrs["wm"].shape[1])
+        self.s_pad = 64 if self.n_tokens <= 64 else 128
+        w = _lib.AttnWeights(**{k: arrs[k].ctypes.data_as(C.c_void_p) for k in _ATTN_KEYS})
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = C.c_void_p()
+        check(lib().pfem_attn_create(self.n_channels, self.n_tokens, int(n_heads), float(scale), C.byref(w),
+                                     C.c_void_p(stream.cuda_stream), C.byref(h)))
+        self.handle = h
+
+    def forward(self, x, xt=None, m=None, tokens=False):
+        """x: bf16 CUDA tensor [N][C].  Returns xt (bf16 [N][C]); with tokens=True also the
+        slice weights m (bf16 [N][S_pad]) and the tokens Z, Z^t (float32 [S][C])."""
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.bfloat16 and x.is_contiguous()
+                and x.dim() == 2 and x.shape[1] == self.n_channels):
+            raise TypeError("x must be a contiguous bf16 CUDA tensor of shape [N, %d]" % self.n_channels)
+        n = int(x.shape[0])
+        if xt is None:
+            xt = torch.empty_like(x)
+        if m is None and tokens:
+            m = torch.empty((n, self.s_pad), dtype=torch.bfloat16, device=x.device)
+        z = zt = None
+        if tokens:
+            z = torch.zeros((self.n_tokens, self.n_channels), dtype=torch.float32, device=x.device)
+            zt = torch.zeros_like(z)
+        check(lib().pfem_attn_forward(self.handle, n, C.c_void_p(x.data_ptr()), _dev(xt, x.numel(), "xt"),
+                                      None if m is None else _dev(m, n * self.s_pad, "m"),
+                                      None if z is None else C.c_void_p(z.data_ptr()),
+                                      None if zt is None else C.c_void_p(zt.data_ptr())))
+        return (xt, m, z, zt) if tokens else xt
+
+    def sync(self):
+        check(lib().pfem_attn_sync(self.handle))
+
+    def set_timing(self, on):
+        check(lib().pfem_attn_set_timing(self.handle, int(bool(on))))
+
+    def kernel_ms(self):
+        """Durations (ms) of the slice, token-sum, token-attention and deslice kernels of the
+        last timed forward."""
+        ms = (C.c_double * 4)()
+        check(lib().pfem_attn_kernel_ms(self.handle, ms))
+        return dict(zip(("slice", "reduce", "tokens", "deslice"), list(ms)))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pfem_attn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pfem_attn_create(params, n_heads, scale=1.0, stream=None):
+    return Attention(params, n_heads, scale, stream)
+
+
+def pfem_attn_forward(attn, x, xt=None, m=None, tokens=False):
+    return attn.forward(x, xt, m, tokens)
+
+
+def pfem_attn_sync(attn):
+    attn.sync()
+
+
+def pfem_attn_destroy(attn):
+    attn.close()
