@@ -110,8 +110,11 @@ pfem_status launch_batch(const BatchDev& B, int n_blocks, int n_meshes, const fl
 
 // ---- serving: one shared PCG step over all resident solves ------------------------------
 
-__global__ void __launch_bounds__(kTileThreads) serve_apply_kernel(const ReqDev* reqs, const int2* btile, int max_local,
-                                                               int slot_cap, int step_cap) {
+// One kernel per material kind, so that each gets the register budget (and resident CTAs
+// per SM) of its own arithmetic, as the single-solve tile kernels do.
+template <int KIND>
+__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<KIND, float>())
+    serve_apply_kernel(const ReqDev* reqs, const int2* btile, int max_local, int slot_cap, int step_cap) {
   extern __shared__ __align__(32) unsigned char smem[];
   __shared__ ReqDev sR;
   const int2 bt = btile[blockIdx.x];
@@ -122,10 +125,8 @@ __global__ void __launch_bounds__(kTileThreads) serve_apply_kernel(const ReqDev*
   a.y = sR.q;
   a.load_scale = 1.0;
   a.pcg = sR.pcg;
-  const SmemLayout<float> L = smem_layout<float>(max_local, slot_cap, step_cap, true, true);
-  constexpr int OPS = OP_TANGENT | OP_PCG;
-  if (sR.plan.kind == PFEM_LINEAR) process_tile<3, K_LIN, OPS, double, float>(sR.plan, a, bt.y, smem, L);
-  else process_tile<3, K_NH, OPS, double, float>(sR.plan, a, bt.y, smem, L);
+  const SmemLayout<float> L = smem_layout<float>(max_local, slot_cap, step_cap, KIND == K_NH, true);
+  process_tile<3, KIND, OP_TANGENT | OP_PCG, double, float>(sR.plan, a, bt.y, smem, L);
 }
 
 // x += alpha p; r -= alpha q; r.z and r.r reduced over the solve's own blocks (fixed order),
@@ -186,15 +187,26 @@ __global__ void __launch_bounds__(256) serve_update_kernel(const ReqDev* reqs, c
   }
 }
 
-pfem_status launch_serve_step(const ReqDev* reqs, const int2* btile, int n_apply_blocks, const int* ublk,
-                              int n_update_blocks, int max_local, int slot_cap, int step_cap, cudaStream_t s) {
-  const SmemLayout<float> L = smem_layout<float>(max_local, slot_cap, step_cap, true, true);
-  static int max_dyn = 0;
-  pfem_status st = allow_dynamic_smem(serve_apply_kernel, L.total, &max_dyn);
-  if (st) return st;
-  if (n_apply_blocks > 0) {
-    serve_apply_kernel<<<n_apply_blocks, kTileThreads, L.total, s>>>(reqs, btile, max_local, slot_cap, step_cap);
-    PFEM_COUNT_LAUNCH();
+pfem_status launch_serve_step(const ReqDev* reqs, const int2* btile, const ServeTiles (&tiles)[2], const int* ublk,
+                              int n_update_blocks, cudaStream_t s) {
+  static int max_dyn[2] = {0, 0};
+  const int2* bt = btile;
+  for (int kind = 0; kind < 2; ++kind) {
+    const ServeTiles& T = tiles[kind];
+    const SmemLayout<float> L = smem_layout<float>(T.max_local, T.slot_cap, T.step_cap, kind == K_NH, true);
+    pfem_status st = kind == K_LIN ? allow_dynamic_smem(serve_apply_kernel<K_LIN>, L.total, &max_dyn[0])
+                                   : allow_dynamic_smem(serve_apply_kernel<K_NH>, L.total, &max_dyn[1]);
+    if (st) return st;
+    if (T.n_blocks > 0) {
+      if (kind == K_LIN)
+        serve_apply_kernel<K_LIN><<<T.n_blocks, kTileThreads, L.total, s>>>(reqs, bt, T.max_local, T.slot_cap,
+                                                                             T.step_cap);
+      else
+        serve_apply_kernel<K_NH><<<T.n_blocks, kTileThreads, L.total, s>>>(reqs, bt, T.max_local, T.slot_cap,
+                                                                            T.step_cap);
+      PFEM_COUNT_LAUNCH();
+    }
+    bt += T.n_blocks;
   }
   if (n_update_blocks > 0) {
     serve_update_kernel<<<n_update_blocks, 256, 0, s>>>(reqs, ublk);

@@ -321,10 +321,18 @@ struct ReqDev {
   unsigned int* ucount;    // last-block ticket of the update
 };
 
-// Shared PCG step over many solves: fused apply (one CTA per (solve, tile)) then update
-// (one CTA range per solve). btile: (solve, tile) per apply block; ublk: solve per update block.
-pfem_status launch_serve_step(const ReqDev* reqs, const int2* btile, int n_apply_blocks, const int* ublk,
-                              int n_update_blocks, int max_local, int slot_cap, int step_cap, cudaStream_t s);
+// Apply blocks of one material kind in a shared serving step, and the largest tile shape
+// among their solves (sizes the shared memory of that kind's launch).
+struct ServeTiles {
+  int n_blocks = 0, max_local = 1, slot_cap = 4, step_cap = 1;
+};
+
+// Shared PCG step over many solves: fused apply (one CTA per (solve, tile); a launch for the
+// linear solves' tiles, then one for the Neo-Hookean solves') and update (one CTA range per
+// solve). btile: (solve, tile) per apply block, linear blocks first; ublk: solve per update
+// block.
+pfem_status launch_serve_step(const ReqDev* reqs, const int2* btile, const ServeTiles (&tiles)[2], const int* ublk,
+                              int n_update_blocks, cudaStream_t s);
 
 // Blocks the update launch gives a solve of n DOFs (depends on n only).
 inline int serve_update_blocks(int64_t n) {

@@ -166,7 +166,8 @@ struct pfem_server_s {
   StateSlot* d_slots = nullptr;
   StateSlot* h_slots = nullptr;
   size_t cap_reqs = 0, cap_btile = 0, cap_ublk = 0;
-  int n_apply = 0, n_update = 0, max_local = 1, slot_cap = 4, step_cap = 1;
+  ServeTiles tiles[2];  // linear, Neo-Hookean apply blocks
+  int n_update = 0;
   std::vector<int> active_index;   // position of each active request in the tables
   // one chunk (kChunk shared steps, the state gather and its read-back) captured as a CUDA
   // graph for the current tables; captured again whenever the tables change
@@ -498,12 +499,12 @@ bool advance(pfem_server_s* S, Request* R, const StateSlot& sl) {
 pfem_status rebuild_tables(pfem_server_s* S) {
   const int na = (int)S->active.size();
   std::vector<ReqDev> reqs((size_t)na);
-  std::vector<int2> btile;
+  std::vector<int2> btile_k[2];
   std::vector<int> ublk;
+  ServeTiles tiles[2];
   std::vector<PcgState*> stp((size_t)na);
   std::vector<double*> auxp((size_t)na);
   std::vector<int32_t*> invp((size_t)na);
-  int max_local = 1, slot_cap = 4, step_cap = 1;
   for (int i = 0; i < na; ++i) {
     Request* R = S->active[(size_t)i];
     ReqDev& d = reqs[(size_t)i];
@@ -524,15 +525,21 @@ pfem_status rebuild_tables(pfem_server_s* S) {
     d.nublk = R->nublk;
     d.upart = R->upart;
     d.ucount = R->ucount;
-    for (int t = 0; t < d.plan.n_tiles; ++t) btile.push_back(make_int2(i, t));
+    const int kind = d.plan.kind == PFEM_LINEAR ? 0 : 1;
+    for (int t = 0; t < d.plan.n_tiles; ++t) btile_k[kind].push_back(make_int2(i, t));
     for (int k = 0; k < R->nublk; ++k) ublk.push_back(i);
-    max_local = std::max(max_local, d.plan.max_local);
-    slot_cap = std::max(slot_cap, d.plan.slot_cap);
-    step_cap = std::max(step_cap, d.plan.step_cap);
+    ServeTiles& T = tiles[kind];
+    T.max_local = std::max(T.max_local, d.plan.max_local);
+    T.slot_cap = std::max(T.slot_cap, d.plan.slot_cap);
+    T.step_cap = std::max(T.step_cap, d.plan.step_cap);
     stp[(size_t)i] = R->st;
     auxp[(size_t)i] = R->aux;
     invp[(size_t)i] = R->mesh->plan.inverted;
   }
+  tiles[0].n_blocks = (int)btile_k[0].size();
+  tiles[1].n_blocks = (int)btile_k[1].size();
+  std::vector<int2> btile(btile_k[0]);  // linear blocks first
+  btile.insert(btile.end(), btile_k[1].begin(), btile_k[1].end());
   PFEM_CUDA(cudaStreamSynchronize(S->stream));  // the old tables are no longer read
   pfem_status st;
   size_t cap_r = S->cap_reqs, cap_bt = S->cap_btile, cap_u = S->cap_ublk;
@@ -566,11 +573,9 @@ pfem_status rebuild_tables(pfem_server_s* S) {
   if (!btile.empty())
     PFEM_CUDA(cudaMemcpy(S->d_btile, btile.data(), btile.size() * sizeof(int2), cudaMemcpyHostToDevice));
   if (!ublk.empty()) PFEM_CUDA(cudaMemcpy(S->d_ublk, ublk.data(), ublk.size() * sizeof(int), cudaMemcpyHostToDevice));
-  S->n_apply = (int)btile.size();
+  S->tiles[0] = tiles[0];
+  S->tiles[1] = tiles[1];
   S->n_update = (int)ublk.size();
-  S->max_local = max_local;
-  S->slot_cap = slot_cap;
-  S->step_cap = step_cap;
   S->dirty = false;
   return PFEM_OK;
 }
@@ -606,8 +611,7 @@ constexpr int kChunk = 8;  // shared steps between two read-backs of the solves'
 pfem_status enqueue_chunk(pfem_server_s* S, cudaStream_t s) {
   pfem_status st;
   for (int k = 0; k < kChunk; ++k)
-    if ((st = launch_serve_step(S->d_reqs, S->d_btile, S->n_apply, S->d_ublk, S->n_update, S->max_local,
-                                S->slot_cap, S->step_cap, s)))
+    if ((st = launch_serve_step(S->d_reqs, S->d_btile, S->tiles, S->d_ublk, S->n_update, s)))
       return st;
   const int na = (int)S->active.size();
   gather_states_kernel<<<(na + 127) / 128, 128, 0, s>>>(S->d_stp, S->d_auxp, S->d_invp, na, S->d_slots);
@@ -625,8 +629,9 @@ pfem_status capture_chunk(pfem_server_s* S) {
   }
   // a step with no blocks launches nothing but sets the apply kernel's shared-memory limit,
   // which is a function attribute and stays outside the capture
-  pfem_status pre = launch_serve_step(S->d_reqs, S->d_btile, 0, S->d_ublk, 0, S->max_local, S->slot_cap,
-                                      S->step_cap, S->stream);
+  ServeTiles none[2] = {S->tiles[0], S->tiles[1]};
+  none[0].n_blocks = none[1].n_blocks = 0;
+  pfem_status pre = launch_serve_step(S->d_reqs, S->d_btile, none, S->d_ublk, 0, S->stream);
   if (pre != PFEM_OK) return pre;
   const int64_t before = g_kernel_launches;
   PFEM_CUDA(cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal));
