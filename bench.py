@@ -886,7 +886,11 @@ def probe(a):
         ev[1].record()
         ev[1].synchronize()
         attn.sync()
-        print(json.dumps({"probe": "attn", "n": a.n, "forward_us": ev[0].elapsed_time(ev[1]) * 1e3 / a.reps}))
+        attn.set_timing(True)
+        attn.forward(x, xt)
+        k = {q: 1e3 * v for q, v in attn.kernel_ms().items()}
+        print(json.dumps({"probe": "attn", "n": a.n, "forward_us": ev[0].elapsed_time(ev[1]) * 1e3 / a.reps,
+                          "kernel_us": k}))
         attn.close()
         return 0
     p = pi.cube_problem(a.n, seed=2) if a.kind == "linear" else pi.bar_problem(4 * a.n, a.n, a.n, seed=3)

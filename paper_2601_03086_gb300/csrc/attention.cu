@@ -179,14 +179,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
+    // The projection MMA of tile i + 1 is issued as soon as the epilogue has read tile i's
+    // accumulators (B_TFREE), before the slice MMA of tile i waits for the epilogue's
+    // operands (B_EPI), so the epilogues run back to back.
     const uint32_t id1 = idesc_bf16(kTile, CS, false, false);
     const uint32_t id3 = idesc_bf16(kTile, kZCols, true, true);
     const uint32_t ax = smem_addr(sx), aw = smem_addr(sw), aa = smem_addr(sa), ab = smem_addr(sb);
-    bool ok = mbar_wait(&bar[B_WFULL], 0, a.err, kWaitNs);
-    for (int i = 0; ok && i < T; ++i) {
+    auto project = [&](int i) -> bool {
       const int s = i & 1, k = i >> 1;
-      if (!mbar_wait(&bar[B_FULL0 + s], k & 1, a.err, kWaitNs)) break;
-      if (!mbar_wait(&bar[B_TFREE], (i & 1) ^ 1, a.err, kWaitNs)) break;
+      if (!mbar_wait(&bar[B_FULL0 + s], k & 1, a.err, kWaitNs)) return false;
+      if (!mbar_wait(&bar[B_TFREE], (i & 1) ^ 1, a.err, kWaitNs)) return false;
       tc_fence_after();
 #pragma unroll
       for (int kk = 0; kk < kC / 16; ++kk) {
@@ -197,6 +199,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       mma_commit(&bar[B_EMPTY0 + s]);
       mma_commit(&bar[B_MMA]);
+      return true;
+    };
+    bool ok = mbar_wait(&bar[B_WFULL], 0, a.err, kWaitNs) && project(0);
+    for (int i = 0; ok && i < T; ++i) {
+      if (i + 1 < T && !project(i + 1)) break;
       if (!mbar_wait(&bar[B_EPI], i & 1, a.err, kWaitNs)) break;
       tc_fence_after();
 #pragma unroll
@@ -472,33 +479,48 @@ __global__ void __launch_bounds__(256) attn_reduce_kernel(const float* partial, 
 
 constexpr int kMaxHeadDim = 64;
 
-// One CTA per head h: Q_h, K_h, V_h = Z W[:, h d .. h d + d) + b, then per token row an
-// online softmax over the S keys.  Writes Z^t (FP32, [S][C]) and (Z^t)^T in bf16 ([C][S_pad],
-// the deslice's B operand); CTA 0 also writes the normalised tokens Z.
+// One CTA per head h: Z (normalised tokens) staged in shared memory, then Q_h, K_h, V_h =
+// Z W[:, h d .. h d + d) + b (each thread forms 8 rows of one column, one weight load per
+// input channel), then per token row an online softmax over the S keys.  Writes Z^t (FP32,
+// [S][C]) and (Z^t)^T in bf16 ([C][S_pad], the deslice's B operand); CTA 0 also writes Z.
+constexpr int kRowsPerThread = 8;
+
 __global__ void __launch_bounds__(256) attn_tokens_kernel(const float* zsum, const float* wqkv, const float* bqkv,
                                                           int S, int SP, int H, float scale, float* z, float* zt,
                                                           __nv_bfloat16* ztT) {
   extern __shared__ float sh[];
   const int d = kC / H, h = blockIdx.x;
-  float* sq = sh;               // [S][d]
+  float* sz = sh;               // [S][C] normalised tokens
+  float* sq = sz + S * kC;      // [S][d]
   float* sk = sq + S * d;       // [S][d]
   float* sv = sk + S * d;       // [S][d]
-  float* sinv = sv + S * d;     // [S]: 1 / token weight (0 for a zero-weight token)
-  for (int j = threadIdx.x; j < S; j += blockDim.x) {
+  for (int e = threadIdx.x; e < S * kC; e += blockDim.x) {
+    const int j = e / kC, c = e % kC;
     const float w = zsum[j * kPartPitch + kC];
-    sinv[j] = w > 0.0f ? 1.0f / w : 0.0f;
+    const float v = w > 0.0f ? zsum[j * kPartPitch + c] / w : 0.0f;
+    sz[e] = v;
+    if (h == 0) z[e] = v;
   }
   __syncthreads();
-  if (h == 0)
-    for (int e = threadIdx.x; e < S * kC; e += blockDim.x) z[e] = zsum[(e / kC) * kPartPitch + e % kC] * sinv[e / kC];
-  for (int e = threadIdx.x; e < 3 * S * d; e += blockDim.x) {
-    const int m = e / (S * d), r = e % (S * d), j = r / d, t = r % d;
-    const int col = h * d + t;
-    const float* W = wqkv + static_cast<int64_t>(m) * kC * kC;
-    const float* zr = zsum + j * kPartPitch;
-    float acc = 0.0f;
-    for (int c = 0; c < kC; ++c) acc = fmaf(zr[c], W[c * kC + col], acc);
-    sh[e] = fmaf(acc, sinv[j], bqkv[m * kC + col]);  // (Z_num W)_jt / w_j = (Z W)_jt
+  const int groups = (S + kRowsPerThread - 1) / kRowsPerThread;
+  for (int e = threadIdx.x; e < 3 * d * groups; e += blockDim.x) {
+    const int m = e / (d * groups), r = e % (d * groups), t = r % d, g = r / d;
+    const int col = h * d + t, j0 = g * kRowsPerThread;
+    const float* W = wqkv + static_cast<int64_t>(m) * kC * kC + col;
+    float acc[kRowsPerThread];
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q) acc[q] = 0.0f;
+    for (int c = 0; c < kC; ++c) {
+      const float wv = __ldg(W + c * kC);
+#pragma unroll
+      for (int q = 0; q < kRowsPerThread; ++q)
+        if (j0 + q < S) acc[q] = fmaf(sz[(j0 + q) * kC + c], wv, acc[q]);
+    }
+    float* dst = (m == 0 ? sq : m == 1 ? sk : sv);
+    const float b = bqkv[m * kC + col];
+#pragma unroll
+    for (int q = 0; q < kRowsPerThread; ++q)
+      if (j0 + q < S) dst[(j0 + q) * d + t] = acc[q] + b;
   }
   __syncthreads();
   for (int a = threadIdx.x; a < S; a += blockDim.x) {
@@ -619,9 +641,9 @@ pfem_status set_smem_attrs() {
     if (r == cudaSuccess)
       r = cudaFuncSetAttribute(attn_deslice_kernel<SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(deslice_smem_bytes<SP>()));
-    if (r == cudaSuccess)  // Q, K, V of one head (S x d each, d <= 64) and the token weights
+    if (r == cudaSuccess)  // the tokens (S x C) and Q, K, V of one head (S x d each, d <= 64)
       r = cudaFuncSetAttribute(attn_tokens_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>((3 * 128 * kMaxHeadDim + 128) * sizeof(float)));
+                               static_cast<int>((128 * kC + 3 * 128 * kMaxHeadDim) * sizeof(float)));
     return r;
   }();
   PFEM_CUDA(e);
@@ -649,7 +671,7 @@ pfem_status launch_forward(pfem_attn_t a, int64_t n, const void* x, void* xt, __
   PFEM_CUDA(cudaGetLastError());
   if (a->timing) PFEM_CUDA(cudaEventRecord(a->ev[2], a->stream));
   const int d = kC / a->H;
-  const size_t tsm = (3 * static_cast<size_t>(a->S) * d + a->S) * sizeof(float);
+  const size_t tsm = (static_cast<size_t>(a->S) * kC + 3 * static_cast<size_t>(a->S) * d) * sizeof(float);
   attn_tokens_kernel<<<a->H, 256, tsm, a->stream>>>(a->zsum, a->wqkv, a->bqkv, a->S, SP, a->H, a->scale, a->z, a->zt,
                                                     a->ztT);
   PFEM_COUNT_LAUNCH();

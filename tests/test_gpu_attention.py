@@ -4,9 +4,9 @@ the FP64 oracle of the Method's subsection "Transolver".
 Bars, from the kernel's storage precision (bf16, unit roundoff u = 2^-9; FP32 elsewhere):
   * against the oracle with the same bf16 roundings applied at the points where the kernel
     stores (U and M before the sums, Z^t before the deslice, X^t on output): slice weights
-    within 1 bf16 ulp (2u relative) plus 2e-6 absolute (the FP32 exponential may move a value
-    across a rounding boundary), tokens Z and Z^t within rel L2 1e-3 (FP32 sums of up to 2^20
-    products, rounding flips), X^t within rel L2 2e-3;
+    within one bf16 ulp (the FP32 logits and exponential may move a value across a rounding
+    boundary), tokens Z and Z^t within rel L2 1e-3 (FP32 sums of up to 2^20 products,
+    rounding flips), X^t within rel L2 2e-3;
   * against the plain FP64 oracle: X^t and Z within rel L2 1e-2 (four bf16 roundings in
     sequence, each at most u = 1.95e-3 relative, first order 4u = 7.8e-3).
 Ragged tails (N not a multiple of the 128-point tile), N < 128, every supported token count
@@ -47,9 +47,11 @@ def _check(params, X, H, scale, got):
     S = params["wm"].shape[1]
     ref = at.physics_attention(X, params, H, scale)
     emu = at.physics_attention(X, params, H, scale, rnd=ai.to_bf16_grid)
-    # slice weights: 1 bf16 ulp of the emulated value, pad columns exactly zero
+    # slice weights: within one bf16 ulp of the emulated value (2^(e - 7) for a value in
+    # [2^e, 2^(e+1))), pad columns exactly zero
     assert np.all(m[:, S:] == 0.0)
-    np.testing.assert_array_less(np.abs(m[:, :S] - emu["M"]), 2.0 ** -8 * np.abs(emu["M"]) + 2e-6)
+    ulp = 2.0 ** (np.floor(np.log2(np.maximum(np.abs(emu["M"]), 1e-30))) - 7)
+    np.testing.assert_array_less(np.abs(m[:, :S] - emu["M"]), ulp * 1.0001 + 1e-12)
     assert rel_l2(z, emu["Z"]) <= 1e-3
     assert rel_l2(zt, emu["Zt"]) <= 1e-3
     assert rel_l2(xt, emu["Xt"]) <= 2e-3
