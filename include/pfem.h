@@ -406,8 +406,8 @@ typedef struct {               /* HOST float arrays, read during pfem_attn_creat
 } pfem_attn_weights;
 
 /* Build a module on the current device with its weights resident. n_channels must be 128;
- * n_tokens a multiple of 16 in [16, 128]; n_heads divides 128 with at most 64 channels per
- * head; calls run on cuda_stream (NULL = legacy default stream).
+ * n_tokens a multiple of 16 in [16, 128]; n_heads 2, 4, 8 or 16 (64, 32, 16 or 8 channels
+ * per head); calls run on cuda_stream (NULL = legacy default stream).
  * Errors: INVALID_ARG (NULL pointer, non-finite weight or scale), UNSUPPORTED (sizes),
  * OUT_OF_MEMORY / CUDA. On error *out is NULL. */
 pfem_status pfem_attn_create(int32_t n_channels, int32_t n_tokens, int32_t n_heads, double scale,

@@ -7,6 +7,7 @@
 //                       M stored (bf16, TMA) for the deslice
 //   reduce              per-CTA partial token sums added in a fixed order
 //   tokens  (FP32)      Z = Z_num / w; Q, K, V = Z W + b; per head softmax(scale Q K^T) V
+//                       (two kernels: the projections, then the heads)
 //   deslice (tcgen05):  X^t = M Z^t                                      one 128 x C MMA/tile
 //
 // Data layout: X, X^t row-major [N][C] bf16; M row-major [N][S_pad] bf16 (S_pad = 64 or 128,
@@ -44,8 +45,12 @@ constexpr int kTile = 128;         // points per tile = MMA M = TMEM lanes
 constexpr int kRegion = kTile * 128;  // one 64-column bf16 region of a 128-row tile (16 KB)
 constexpr int kZCols = 144;        // slice MMA N: C channels, the weight-sum column, zero pad
 constexpr int kPartPitch = 132;    // floats per token row of a CTA partial (C sums, w, pad)
-constexpr int kThreads = 192;      // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kThreads = 192;      // deslice: warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int kEpi = 128;
+// slice: warp 0 TMA, warp 1 MMA, 16 epilogue warps: four per TMEM lane quarter, each taking
+// a quarter of the columns (32 channels of U and S_pad / 4 slice logits of its 32 points)
+constexpr int kSliceEpi = 512;
+constexpr int kSliceThreads = 64 + kSliceEpi;
 constexpr uint64_t kWaitNs = 2000000000ull;  // bounded waits: 2 s
 
 __device__ __forceinline__ bool vote_any(bool pred, uint32_t id, uint32_t count) {
@@ -96,12 +101,13 @@ enum { B_FULL0, B_FULL1, B_EMPTY0, B_EMPTY1, B_WFULL, B_MMA, B_TFREE, B_EPI, B_S
 
 template <int SP>
 constexpr size_t slice_smem_bytes() {
-  return 1024 + 2 * (kC + SP) * 128 + 2 * 2 * kRegion + 2 * kRegion + 3 * kRegion + 256 * 4 + 16 * 8 + 16;
+  return 1024 + 2 * (kC + SP) * 128 + 2 * 2 * kRegion + 2 * kRegion + 3 * kRegion + 256 * 4 + 2 * 4 * kTile * 4 +
+         16 * 8 + 16;
 }
 
 // One persistent CTA per SM; CTA b takes tiles b, b + grid, ...
 template <int SP>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kSliceThreads, 1)
     attn_slice_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
                       const __grid_constant__ CUtensorMap map_m, SliceArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -112,7 +118,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* sa = sx + 4 * kRegion;               // M (MN-major A of the slice MMA): 2 regions
   uint8_t* sb = sa + 2 * kRegion;               // [U | 1] (MN-major B): 3 regions
   float* sbias = reinterpret_cast<float*>(sb + 3 * kRegion);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(sbias + 256);
+  float* xmax = sbias + 256;        // [4][kTile]: per column quarter, partial row maxima
+  float* xsum = xmax + 4 * kTile;   // [4][kTile]: partial row sums
+  uint64_t* bar = reinterpret_cast<uint64_t*>(xsum + 4 * kTile);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 16);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -121,13 +129,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   // constant operand parts: token rows past SP (and all of region 1 when SP = 64) are zero;
   // region 2 of [U | 1] holds the ones column (n = 128) and zeros
-  for (int i = threadIdx.x; i < (2 * kRegion) / 16; i += kThreads) {
+  for (int i = threadIdx.x; i < (2 * kRegion) / 16; i += kSliceThreads) {
     const int r = (i * 16) / kRegion;
     if (r >= SP / 64) reinterpret_cast<uint4*>(sa)[i] = make_uint4(0, 0, 0, 0);
   }
-  for (int i = threadIdx.x; i < kRegion / 16; i += kThreads)
+  for (int i = threadIdx.x; i < kRegion / 16; i += kSliceThreads)
     reinterpret_cast<uint4*>(sb + 2 * kRegion)[i] = make_uint4(0, 0, 0, 0);
-  for (int i = threadIdx.x; i < CS; i += kThreads) sbias[i] = a.bias[i];
+  for (int i = threadIdx.x; i < CS; i += kSliceThreads) sbias[i] = a.bias[i];
   __syncthreads();
   if (threadIdx.x < kTile) {
     const int row = threadIdx.x;  // n = 128 sits in logical chunk 0, element 0 of the row
@@ -140,8 +148,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(&bar[B_EMPTY1], 1);
     mbar_init(&bar[B_WFULL], 1);
     mbar_init(&bar[B_MMA], 1);
-    mbar_init(&bar[B_TFREE], kEpi);
-    mbar_init(&bar[B_EPI], kEpi);
+    mbar_init(&bar[B_TFREE], kSliceEpi);
+    mbar_init(&bar[B_EPI], kSliceEpi);
     mbar_init(&bar[B_SLICE], 1);
     mbar_init(&bar[B_FINAL], 1);
     fence_barrier_init();
@@ -217,8 +225,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     mma_commit(&bar[B_FINAL]);  // all MMAs done before the tensor memory is released
     mbar_wait(&bar[B_FINAL], 0, a.err, kWaitNs);
   } else if (warp >= 2) {
-    // ---------------- epilogue: one thread per point (TMEM lane) ----------------
-    const int q = warp & 3;
+    // ---------------- epilogue: one thread per (point, column quarter) ----------------
+    // Barriers: 1 + q among the four warps of lane quarter q (softmax exchange), 5 and 6
+    // among all epilogue threads (vote on the waits, operands complete before the M store).
+    constexpr int LQ = SP / 4;  // slice logits per thread
+    const int q = warp & 3, part = (warp - 2) >> 2;
     const int row = 32 * q + lane;
     const uint32_t tl = tmem + (static_cast<uint32_t>(32 * q) << 16);
     const bool leader = (warp == 2 && lane == 0);
@@ -230,83 +241,86 @@ __global__ void __launch_bounds__(kThreads, 1)
         ok = mbar_wait(&bar[B_SLICE], (i & 1) ^ 1, a.err, kWaitNs) && ok;  // slice operands free
         bulk_wait_read_all();                                                 // M store has read sa
       }
-      if (vote_any(!ok, 1, kEpi)) {
+      if (vote_any(!ok, 5, kSliceEpi)) {
         failed = true;
         break;
       }
       tc_fence_after();
-      // U + b_U -> bf16 rows of region 0/1 of [U | 1]
-#pragma unroll
-      for (int c = 0; c < kC / 32; ++c) {
-        float u[32];
-        tmem_ld32(tl + 32 * c, u);
-        tmem_ld_wait();
-#pragma unroll
-        for (int e = 0; e < 32; ++e) u[e] += sbias[32 * c + e];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) st_chunk(sb + (c >> 1) * kRegion, row, (c & 1) * 4 + m, u + 8 * m);
-      }
-      float lg[SP];
-#pragma unroll
-      for (int c = 0; c < SP / 32; ++c) {
-        float t[32];
-        tmem_ld32(tl + kC + 32 * c, t);
-#pragma unroll
-        for (int e = 0; e < 32; ++e) lg[32 * c + e] = t[e];
+      float u[32], lg[LQ];
+      tmem_ld32(tl + 32 * part, u);
+      if constexpr (LQ == 32) {
+        tmem_ld32(tl + kC + 32 * part, lg);
+      } else {
+        tmem_ld16(tl + kC + 16 * part, lg);
       }
       tmem_ld_wait();
       tc_fence_before();
       mbar_arrive(&bar[B_TFREE]);
-      // M = softmax over the S tokens (zero rows for points past the end)
-      const bool valid = static_cast<int64_t>(tile) * kTile + row < a.n_points;
-      float mx = -INFINITY;
+      // U + b_U -> bf16, channels 32 part .. 32 part + 31 of the row of [U | 1]
 #pragma unroll
-      for (int j = 0; j < SP; ++j)
-        if (j < S) {
-          lg[j] += sbias[kC + j];
-          mx = fmaxf(mx, lg[j]);
+      for (int e = 0; e < 32; ++e) u[e] += sbias[32 * part + e];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) st_chunk(sb + (part >> 1) * kRegion, row, (part & 1) * 4 + m, u + 8 * m);
+      // M = softmax over the S tokens, the row spread over four threads (zero rows for points
+      // past the end); partial maxima and sums combined in quarter order
+      const int j0 = LQ * part;
+      float pm = -INFINITY;
+#pragma unroll
+      for (int j = 0; j < LQ; ++j)
+        if (j0 + j < S) {
+          lg[j] += sbias[kC + j0 + j];
+          pm = fmaxf(pm, lg[j]);
         }
-      float sum = 0.0f;
+      xmax[part * kTile + row] = pm;
+      named_sync(1 + q, 128);
+      const float mx = fmaxf(fmaxf(xmax[row], xmax[kTile + row]), fmaxf(xmax[2 * kTile + row], xmax[3 * kTile + row]));
+      float ps = 0.0f;
 #pragma unroll
-      for (int j = 0; j < SP; ++j) {
-        lg[j] = j < S ? exp2f((lg[j] - mx) * 1.4426950408889634f) : 0.0f;
-        sum += lg[j];
+      for (int j = 0; j < LQ; ++j) {
+        lg[j] = j0 + j < S ? exp2f((lg[j] - mx) * 1.4426950408889634f) : 0.0f;
+        ps += lg[j];
       }
+      xsum[part * kTile + row] = ps;
+      named_sync(1 + q, 128);
+      const float sum = ((xsum[row] + xsum[kTile + row]) + xsum[2 * kTile + row]) + xsum[3 * kTile + row];
+      const bool valid = static_cast<int64_t>(tile) * kTile + row < a.n_points;
       const float inv = valid ? 1.0f / sum : 0.0f;
 #pragma unroll
-      for (int j = 0; j < SP; ++j) lg[j] *= inv;
+      for (int j = 0; j < LQ; ++j) lg[j] *= inv;
+      if constexpr (LQ == 32) {
 #pragma unroll
-      for (int r = 0; r < SP / 64; ++r)
+        for (int m = 0; m < 4; ++m) st_chunk(sa + (part >> 1) * kRegion, row, (part & 1) * 4 + m, lg + 8 * m);
+      } else {
 #pragma unroll
-        for (int c8 = 0; c8 < 8; ++c8) st_chunk(sa + r * kRegion, row, c8, lg + 64 * r + 8 * c8);
+        for (int m = 0; m < 2; ++m) st_chunk(sa, row, 2 * part + m, lg + 8 * m);
+      }
       fence_async_smem();
       mbar_arrive(&bar[B_EPI]);
-      named_sync(1, kEpi);
+      named_sync(6, kSliceEpi);
       if (leader) {
 #pragma unroll
         for (int r = 0; r < SP / 64; ++r) tma_store_2d(&map_m, sa + r * kRegion, 64 * r, tile * kTile);
         bulk_commit();
       }
     }
-    // this CTA's token sums: lane j of the slice accumulator = token j
+    // this CTA's token sums: lane j of the slice accumulator = token j; quarter `part` of
+    // the columns per thread, the weight sums (column 128) by the first quarter
     bool ok = !failed && mbar_wait(&bar[B_SLICE], (T - 1) & 1, a.err, kWaitNs);
-    if (!vote_any(!ok, 1, kEpi)) {
+    if (!vote_any(!ok, 5, kSliceEpi)) {
       tc_fence_after();
       float* dst = a.partial + (static_cast<int64_t>(blockIdx.x) * S + row) * kPartPitch;
+      float v[32];
+      tmem_ld32(tl + 256 + 32 * part, v);
+      tmem_ld_wait();
+      if (row < S) {
 #pragma unroll
-      for (int c = 0; c < 5; ++c) {
-        float v[32];
-        tmem_ld32(tl + 256 + 32 * c, v);
+        for (int e = 0; e < 32; e += 4)
+          *reinterpret_cast<float4*>(dst + 32 * part + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+      }
+      if (part == 0) {
+        tmem_ld32(tl + 256 + kC, v);
         tmem_ld_wait();
-        if (row < S) {
-          if (c < 4) {
-#pragma unroll
-            for (int e = 0; e < 32; e += 4)
-              *reinterpret_cast<float4*>(dst + 32 * c + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-          } else {
-            *reinterpret_cast<float4*>(dst + 128) = make_float4(v[0], 0.0f, 0.0f, 0.0f);
-          }
-        }
+        if (row < S) *reinterpret_cast<float4*>(dst + kC) = make_float4(v[0], 0.0f, 0.0f, 0.0f);
       }
     }
     if (leader) bulk_wait_all();
@@ -477,86 +491,108 @@ __global__ void __launch_bounds__(256) attn_reduce_kernel(const float* partial, 
 
 // ---- token attention (FP32 CUDA cores; S x C is tiny) -------------------------------------
 
-constexpr int kMaxHeadDim = 64;
+// Q, K, V = Z W + b for all heads, Z = token sums / weight sums: CTA (x, y) forms the 32 x 32
+// block of token rows 32 y .. and columns 32 (x % 4) .. of matrix x / 4 (Q, K, V) from the
+// staged token rows and weight columns; CTA (0, y) also writes those rows of Z.
+__global__ void __launch_bounds__(256) attn_qkv_kernel(const float* zsum, const float* wqkv, const float* bqkv, int S,
+                                                       float* z, float* qkv) {
+  __shared__ float sz[32][kC + 1];
+  __shared__ float sw[kC][33];
+  const int m = blockIdx.x >> 2, c0 = (blockIdx.x & 3) * 32, r0 = blockIdx.y * 32;
+  for (int e = threadIdx.x; e < 32 * kC; e += blockDim.x) {
+    const int j = e / kC, c = e % kC, row = r0 + j;
+    float v = 0.0f;
+    if (row < S) {
+      const float w = zsum[row * kPartPitch + kC];
+      v = w > 0.0f ? zsum[row * kPartPitch + c] / w : 0.0f;
+      if (blockIdx.x == 0) z[row * kC + c] = v;
+    }
+    sz[j][c] = v;
+  }
+  for (int e = threadIdx.x; e < kC * 32; e += blockDim.x) {
+    const int c = e >> 5, t = e & 31;
+    sw[c][t] = wqkv[static_cast<int64_t>(m) * kC * kC + c * kC + c0 + t];
+  }
+  __syncthreads();
+  const int t = threadIdx.x & 31, jb = threadIdx.x >> 5;
+  float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll 8
+  for (int c = 0; c < kC; ++c) {
+    const float w = sw[c][t];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc[k] = fmaf(sz[jb + 8 * k][c], w, acc[k]);
+  }
+  const float b = bqkv[m * kC + c0 + t];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int row = r0 + jb + 8 * k;
+    if (row < S) qkv[(static_cast<int64_t>(m) * S + row) * kC + c0 + t] = acc[k] + b;
+  }
+}
 
-// One CTA per head h: Z (normalised tokens) staged in shared memory, then Q_h, K_h, V_h =
-// Z W[:, h d .. h d + d) + b (each thread forms 8 rows of one column, one weight load per
-// input channel), then per token row an online softmax over the S keys.  Writes Z^t (FP32,
-// [S][C]) and (Z^t)^T in bf16 ([C][S_pad], the deslice's B operand); CTA 0 also writes Z.
-constexpr int kRowsPerThread = 8;
-
-__global__ void __launch_bounds__(256) attn_tokens_kernel(const float* zsum, const float* wqkv, const float* bqkv,
-                                                          int S, int SP, int H, float scale, float* z, float* zt,
-                                                          __nv_bfloat16* ztT) {
+// Per head h (D = C / H channels): CTA (h, y) takes the query tokens 32 y .. 32 y + 31, four
+// threads per query, each running an online softmax over the keys b = part, part + 4, ...;
+// the four partial (max, sum, output) triples are merged by shuffles in a fixed order.
+// Writes Z^t (FP32, [S][C]) and (Z^t)^T in bf16 ([C][S_pad], the deslice's B operand).
+template <int D>
+__global__ void __launch_bounds__(128) attn_heads_kernel(const float* qkv, int S, int SP, float scale, float* zt,
+                                                         __nv_bfloat16* ztT) {
   extern __shared__ float sh[];
-  const int d = kC / H, h = blockIdx.x;
-  float* sz = sh;               // [S][C] normalised tokens
-  float* sq = sz + S * kC;      // [S][d]
-  float* sk = sq + S * d;       // [S][d]
-  float* sv = sk + S * d;       // [S][d]
-  for (int e = threadIdx.x; e < S * kC; e += blockDim.x) {
-    const int j = e / kC, c = e % kC;
-    const float w = zsum[j * kPartPitch + kC];
-    const float v = w > 0.0f ? zsum[j * kPartPitch + c] / w : 0.0f;
-    sz[e] = v;
-    if (h == 0) z[e] = v;
+  float* sk = sh;          // [S][D]
+  float* sv = sh + S * D;  // [S][D]
+  const int h = blockIdx.x, a = blockIdx.y * 32 + (threadIdx.x >> 2), part = threadIdx.x & 3;
+  for (int e = threadIdx.x; e < S * D; e += blockDim.x) {
+    const int b = e / D, t = e % D;
+    sk[e] = qkv[(static_cast<int64_t>(S) + b) * kC + h * D + t];
+    sv[e] = qkv[(2 * static_cast<int64_t>(S) + b) * kC + h * D + t];
   }
   __syncthreads();
-  const int groups = (S + kRowsPerThread - 1) / kRowsPerThread;
-  for (int e = threadIdx.x; e < 3 * d * groups; e += blockDim.x) {
-    const int m = e / (d * groups), r = e % (d * groups), t = r % d, g = r / d;
-    const int col = h * d + t, j0 = g * kRowsPerThread;
-    const float* W = wqkv + static_cast<int64_t>(m) * kC * kC + col;
-    float acc[kRowsPerThread];
+  float qa[D], o[D];
 #pragma unroll
-    for (int q = 0; q < kRowsPerThread; ++q) acc[q] = 0.0f;
-    for (int c = 0; c < kC; ++c) {
-      const float wv = __ldg(W + c * kC);
-#pragma unroll
-      for (int q = 0; q < kRowsPerThread; ++q)
-        if (j0 + q < S) acc[q] = fmaf(sz[(j0 + q) * kC + c], wv, acc[q]);
-    }
-    float* dst = (m == 0 ? sq : m == 1 ? sk : sv);
-    const float b = bqkv[m * kC + col];
-#pragma unroll
-    for (int q = 0; q < kRowsPerThread; ++q)
-      if (j0 + q < S) dst[(j0 + q) * d + t] = acc[q] + b;
+  for (int t = 0; t < D; ++t) {
+    qa[t] = a < S ? qkv[static_cast<int64_t>(a) * kC + h * D + t] * scale : 0.0f;
+    o[t] = 0.0f;
   }
-  __syncthreads();
-  for (int a = threadIdx.x; a < S; a += blockDim.x) {
-    float qa[kMaxHeadDim], o[kMaxHeadDim];
+  float mx = -INFINITY, l = 0.0f;
+  for (int b = part; b < S; b += 4) {
+    float s = 0.0f;
 #pragma unroll
-    for (int t = 0; t < kMaxHeadDim; ++t) {
-      qa[t] = t < d ? sq[a * d + t] * scale : 0.0f;
-      o[t] = 0.0f;
+    for (int t = 0; t < D; ++t) s = fmaf(qa[t], sk[b * D + t], s);
+    if (s > mx) {
+      const float f = expf(mx - s);
+      l *= f;
+#pragma unroll
+      for (int t = 0; t < D; ++t) o[t] *= f;
+      mx = s;
     }
-    float mx = -INFINITY, l = 0.0f;
-    for (int b = 0; b < S; ++b) {
-      float s = 0.0f;
+    const float w = expf(s - mx);
+    l += w;
 #pragma unroll
-      for (int t = 0; t < kMaxHeadDim; ++t)
-        if (t < d) s = fmaf(qa[t], sk[b * d + t], s);
-      if (s > mx) {
-        const float f = expf(mx - s);
-        l *= f;
+    for (int t = 0; t < D; ++t) o[t] = fmaf(w, sv[b * D + t], o[t]);
+  }
 #pragma unroll
-        for (int t = 0; t < kMaxHeadDim; ++t) o[t] *= f;
-        mx = s;
-      }
-      const float w = expf(s - mx);
-      l += w;
+  for (int off = 1; off <= 2; off <<= 1) {
+    const float m2 = __shfl_xor_sync(0xffffffffu, mx, off);
+    const float l2 = __shfl_xor_sync(0xffffffffu, l, off);
+    const float mn = fmaxf(mx, m2);
+    const float f1 = mx == -INFINITY ? 0.0f : expf(mx - mn);
+    const float f2 = m2 == -INFINITY ? 0.0f : expf(m2 - mn);
+    l = __fadd_rn(__fmul_rn(l, f1), __fmul_rn(l2, f2));
 #pragma unroll
-      for (int t = 0; t < kMaxHeadDim; ++t)
-        if (t < d) o[t] = fmaf(w, sv[b * d + t], o[t]);
+    for (int t = 0; t < D; ++t) {
+      const float o2 = __shfl_xor_sync(0xffffffffu, o[t], off);
+      o[t] = __fadd_rn(__fmul_rn(o[t], f1), __fmul_rn(o2, f2));
     }
+    mx = mn;
+  }
+  if (part == 0 && a < S) {
     const float il = 1.0f / l;
 #pragma unroll
-    for (int t = 0; t < kMaxHeadDim; ++t)
-      if (t < d) {
-        const float v = o[t] * il;
-        zt[a * kC + h * d + t] = v;
-        ztT[(h * d + t) * SP + a] = __float2bfloat16_rn(v);
-      }
+    for (int t = 0; t < D; ++t) {
+      const float v = o[t] * il;
+      zt[a * kC + h * D + t] = v;
+      ztT[(h * D + t) * SP + a] = __float2bfloat16_rn(v);
+    }
   }
 }
 
@@ -581,6 +617,7 @@ struct pfem_attn_s {
   float* zsum = nullptr;          // [S][kPartPitch]
   float* z = nullptr;             // [S][C]
   float* zt = nullptr;            // [S][C]
+  float* qkv = nullptr;            // [3][S][C]: Q, K, V
   __nv_bfloat16* ztT = nullptr;   // [C][SP]
   __nv_bfloat16* mbuf = nullptr;  // [mbuf_rows][SP] workspace for M when the caller gives none
   int64_t mbuf_rows = 0;
@@ -641,9 +678,9 @@ pfem_status set_smem_attrs() {
     if (r == cudaSuccess)
       r = cudaFuncSetAttribute(attn_deslice_kernel<SP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(deslice_smem_bytes<SP>()));
-    if (r == cudaSuccess)  // the tokens (S x C) and Q, K, V of one head (S x d each, d <= 64)
-      r = cudaFuncSetAttribute(attn_tokens_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>((128 * kC + 3 * 128 * kMaxHeadDim) * sizeof(float)));
+    if (r == cudaSuccess)  // K and V of one head, S x 64 each at most
+      r = cudaFuncSetAttribute(attn_heads_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(2 * 128 * 64 * sizeof(float)));
     return r;
   }();
   PFEM_CUDA(e);
@@ -662,7 +699,7 @@ pfem_status launch_forward(pfem_attn_t a, int64_t n, const void* x, void* xt, __
   const int grid = std::min(a->n_sm, n_tiles);
   SliceArgs sa{n, n_tiles, a->S, a->bias, a->partial, a->err};
   if (a->timing) PFEM_CUDA(cudaEventRecord(a->ev[0], a->stream));
-  attn_slice_kernel<SP><<<grid, attn::kThreads, slice_smem_bytes<SP>(), a->stream>>>(mx, a->map_w, mm, sa);
+  attn_slice_kernel<SP><<<grid, kSliceThreads, slice_smem_bytes<SP>(), a->stream>>>(mx, a->map_w, mm, sa);
   PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   if (a->timing) PFEM_CUDA(cudaEventRecord(a->ev[1], a->stream));
@@ -670,10 +707,17 @@ pfem_status launch_forward(pfem_attn_t a, int64_t n, const void* x, void* xt, __
   PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   if (a->timing) PFEM_CUDA(cudaEventRecord(a->ev[2], a->stream));
-  const int d = kC / a->H;
-  const size_t tsm = (static_cast<size_t>(a->S) * kC + 3 * static_cast<size_t>(a->S) * d) * sizeof(float);
-  attn_tokens_kernel<<<a->H, 256, tsm, a->stream>>>(a->zsum, a->wqkv, a->bqkv, a->S, SP, a->H, a->scale, a->z, a->zt,
-                                                    a->ztT);
+  attn_qkv_kernel<<<dim3(12, (a->S + 31) / 32), 256, 0, a->stream>>>(a->zsum, a->wqkv, a->bqkv, a->S, a->z, a->qkv);
+  PFEM_COUNT_LAUNCH();
+  PFEM_CUDA(cudaGetLastError());
+  const dim3 hg(a->H, (a->S + 31) / 32);
+  const size_t hsm = 2 * static_cast<size_t>(a->S) * (kC / a->H) * sizeof(float);
+  switch (a->H) {
+    case 2: attn_heads_kernel<64><<<hg, 128, hsm, a->stream>>>(a->qkv, a->S, SP, a->scale, a->zt, a->ztT); break;
+    case 4: attn_heads_kernel<32><<<hg, 128, hsm, a->stream>>>(a->qkv, a->S, SP, a->scale, a->zt, a->ztT); break;
+    case 8: attn_heads_kernel<16><<<hg, 128, hsm, a->stream>>>(a->qkv, a->S, SP, a->scale, a->zt, a->ztT); break;
+    default: attn_heads_kernel<8><<<hg, 128, hsm, a->stream>>>(a->qkv, a->S, SP, a->scale, a->zt, a->ztT); break;
+  }
   PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   DesliceArgs da{n_tiles, a->err};
@@ -695,6 +739,7 @@ void release(pfem_attn_t a) {
   cudaFree(a->zsum);
   cudaFree(a->z);
   cudaFree(a->zt);
+  cudaFree(a->qkv);
   cudaFree(a->ztT);
   cudaFree(a->mbuf);
   cudaFree(a->err);
@@ -724,9 +769,8 @@ extern "C" pfem_status pfem_attn_create(int32_t n_channels, int32_t n_tokens, in
     set_error("pfem_attn_create: tokens must be a multiple of 16 in [16, 128] (got %d)", n_tokens);
     return PFEM_ERR_UNSUPPORTED;
   }
-  if (n_heads < 2 || kC % n_heads || kC / n_heads > kMaxHeadDim) {
-    set_error("pfem_attn_create: heads must divide %d with at most %d channels each (got %d)", kC, kMaxHeadDim,
-              n_heads);
+  if (n_heads != 2 && n_heads != 4 && n_heads != 8 && n_heads != 16) {
+    set_error("pfem_attn_create: heads must be 2, 4, 8 or 16 (got %d)", n_heads);
     return PFEM_ERR_UNSUPPORTED;
   }
   if (!std::isfinite(scale)) {
@@ -770,6 +814,7 @@ extern "C" pfem_status pfem_attn_create(int32_t n_channels, int32_t n_tokens, in
   alloc(&a->zsum, static_cast<size_t>(S) * kPartPitch * sizeof(float));
   alloc(&a->z, static_cast<size_t>(S) * kC * sizeof(float));
   alloc(&a->zt, static_cast<size_t>(S) * kC * sizeof(float));
+  alloc(&a->qkv, 3 * static_cast<size_t>(S) * kC * sizeof(float));
   alloc(&a->ztT, static_cast<size_t>(kC) * SP * 2);
   alloc(&a->err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(a->wcat, wcat.data(), wcat.size() * 2, cudaMemcpyHostToDevice);
