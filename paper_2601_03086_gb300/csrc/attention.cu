@@ -1,12 +1,14 @@
 // Physics attention of the Transolver backbone (Method, subsection "Transolver") on the
 // sm_103a tensor cores.  Forward pass for N points with C = 128 channels and S tokens:
 //
-//   slice   (tcgen05):  [U | logits] = X [W_U | W_M] + [b_U | b_M]      one 128 x (C+S) MMA/tile
+//   slice   (tcgen05):  [U' | logits] = X [W_U | W_M] + [0 | b_M]     one 128 x (C+S) MMA/tile
 //                       M = softmax_S(logits)                            epilogue, FP32
-//                       [Z_num | w] += M^T [U | 1]                       one 128 x 144 MMA/tile
+//                       [Z_num | w] += M^T [U' | 1]                      one 128 x 144 MMA/tile
 //                       M stored (bf16, TMA) for the deslice
 //   reduce              per-CTA partial token sums added in a fixed order
-//   tokens  (FP32)      Z = Z_num / w; Q, K, V = Z W + b; per head softmax(scale Q K^T) V
+//   tokens  (FP32)      Z = Z_num / w + b_U (the weights sum to w, so the bias of U moves
+//                       out of the per-point work); Q, K, V = Z W + b; per head
+//                       softmax(scale Q K^T) V
 //                       (two kernels: the projections, then the heads)
 //   deslice (tcgen05):  X^t = M Z^t                                      one 128 x C MMA/tile
 //
@@ -148,8 +150,8 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
     mbar_init(&bar[B_EMPTY1], 1);
     mbar_init(&bar[B_WFULL], 1);
     mbar_init(&bar[B_MMA], 1);
-    mbar_init(&bar[B_TFREE], kSliceEpi);
-    mbar_init(&bar[B_EPI], kSliceEpi);
+    mbar_init(&bar[B_TFREE], kSliceEpi / 32);  // one arrival per epilogue warp
+    mbar_init(&bar[B_EPI], kSliceEpi / 32);
     mbar_init(&bar[B_SLICE], 1);
     mbar_init(&bar[B_FINAL], 1);
     fence_barrier_init();
@@ -236,10 +238,13 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
     bool failed = false;
     for (int i = 0; i < T; ++i) {
       const int tile = static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x);
-      bool ok = mbar_wait(&bar[B_MMA], i & 1, a.err, kWaitNs);
+      // one thread waits (the others sleep in the vote barrier, which orders them after it):
+      // accumulators ready, slice operands free, the previous M store has read sa
+      bool ok = true;
       if (leader) {
-        ok = mbar_wait(&bar[B_SLICE], (i & 1) ^ 1, a.err, kWaitNs) && ok;  // slice operands free
-        bulk_wait_read_all();                                                 // M store has read sa
+        ok = mbar_wait(&bar[B_MMA], i & 1, a.err, kWaitNs);
+        ok = ok && mbar_wait(&bar[B_SLICE], (i & 1) ^ 1, a.err, kWaitNs);
+        bulk_wait_read_all();
       }
       if (vote_any(!ok, 5, kSliceEpi)) {
         failed = true;
@@ -255,10 +260,10 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
       }
       tmem_ld_wait();
       tc_fence_before();
-      mbar_arrive(&bar[B_TFREE]);
-      // U + b_U -> bf16, channels 32 part .. 32 part + 31 of the row of [U | 1]
-#pragma unroll
-      for (int e = 0; e < 32; ++e) u[e] += sbias[32 * part + e];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar[B_TFREE]);
+      // X W_U -> bf16, channels 32 part .. 32 part + 31 of the row of [U | 1]; b_U is added to
+      // the tokens instead (sum_I M_IJ (X_I W_U + b_U) / sum_I M_IJ = Z'_J + b_U)
 #pragma unroll
       for (int m = 0; m < 4; ++m) st_chunk(sb + (part >> 1) * kRegion, row, (part & 1) * 4 + m, u + 8 * m);
       // M = softmax over the S tokens, the row spread over four threads (zero rows for points
@@ -295,7 +300,8 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
         for (int m = 0; m < 2; ++m) st_chunk(sa, row, 2 * part + m, lg + 8 * m);
       }
       fence_async_smem();
-      mbar_arrive(&bar[B_EPI]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar[B_EPI]);
       named_sync(6, kSliceEpi);
       if (leader) {
 #pragma unroll
@@ -305,7 +311,8 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
     }
     // this CTA's token sums: lane j of the slice accumulator = token j; quarter `part` of
     // the columns per thread, the weight sums (column 128) by the first quarter
-    bool ok = !failed && mbar_wait(&bar[B_SLICE], (T - 1) & 1, a.err, kWaitNs);
+    bool ok = !failed;
+    if (leader && ok) ok = mbar_wait(&bar[B_SLICE], (T - 1) & 1, a.err, kWaitNs);
     if (!vote_any(!ok, 5, kSliceEpi)) {
       tc_fence_after();
       float* dst = a.partial + (static_cast<int64_t>(blockIdx.x) * S + row) * kPartPitch;
@@ -491,11 +498,11 @@ __global__ void __launch_bounds__(256) attn_reduce_kernel(const float* partial, 
 
 // ---- token attention (FP32 CUDA cores; S x C is tiny) -------------------------------------
 
-// Q, K, V = Z W + b for all heads, Z = token sums / weight sums: CTA (x, y) forms the 32 x 32
+// Q, K, V = Z W + b for all heads, Z = token sums / weight sums + b_U: CTA (x, y) forms the 32 x 32
 // block of token rows 32 y .. and columns 32 (x % 4) .. of matrix x / 4 (Q, K, V) from the
 // staged token rows and weight columns; CTA (0, y) also writes those rows of Z.
-__global__ void __launch_bounds__(256) attn_qkv_kernel(const float* zsum, const float* wqkv, const float* bqkv, int S,
-                                                       float* z, float* qkv) {
+__global__ void __launch_bounds__(256) attn_qkv_kernel(const float* zsum, const float* bias_u, const float* wqkv,
+                                                       const float* bqkv, int S, float* z, float* qkv) {
   __shared__ float sz[32][kC + 1];
   __shared__ float sw[kC][33];
   const int m = blockIdx.x >> 2, c0 = (blockIdx.x & 3) * 32, r0 = blockIdx.y * 32;
@@ -504,7 +511,7 @@ __global__ void __launch_bounds__(256) attn_qkv_kernel(const float* zsum, const 
     float v = 0.0f;
     if (row < S) {
       const float w = zsum[row * kPartPitch + kC];
-      v = w > 0.0f ? zsum[row * kPartPitch + c] / w : 0.0f;
+      v = w > 0.0f ? zsum[row * kPartPitch + c] / w + bias_u[c] : 0.0f;
       if (blockIdx.x == 0) z[row * kC + c] = v;
     }
     sz[j][c] = v;
@@ -707,7 +714,8 @@ pfem_status launch_forward(pfem_attn_t a, int64_t n, const void* x, void* xt, __
   PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   if (a->timing) PFEM_CUDA(cudaEventRecord(a->ev[2], a->stream));
-  attn_qkv_kernel<<<dim3(12, (a->S + 31) / 32), 256, 0, a->stream>>>(a->zsum, a->wqkv, a->bqkv, a->S, a->z, a->qkv);
+  attn_qkv_kernel<<<dim3(12, (a->S + 31) / 32), 256, 0, a->stream>>>(a->zsum, a->bias, a->wqkv, a->bqkv, a->S, a->z,
+                                                                      a->qkv);
   PFEM_COUNT_LAUNCH();
   PFEM_CUDA(cudaGetLastError());
   const dim3 hg(a->H, (a->S + 31) / 32);
