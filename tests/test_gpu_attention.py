@@ -2,8 +2,8 @@
 the FP64 oracle of the Method's subsection "Transolver".
 
 Bars, from the kernel's storage precision (bf16, unit roundoff u = 2^-9; FP32 elsewhere):
-  * against the oracle with the same bf16 roundings applied at the points where the kernel
-    stores (U and M before the sums, Z^t before the deslice, X^t on output): slice weights
+  * against the oracle's steps with the kernel's bf16 roundings (X W_U and M before the sums,
+    b_U added to the tokens, Z^t before the deslice, X^t on output): slice weights
     within one bf16 ulp (the FP32 logits and exponential may move a value across a rounding
     boundary), tokens Z and Z^t within rel L2 1e-3 (FP32 sums of up to 2^20 products,
     rounding flips), X^t within rel L2 2e-3;
@@ -42,11 +42,24 @@ def _run(P, params, X, H, scale, tokens=True):
     return out.float().cpu().numpy()
 
 
+def _emulated(X, params, H, scale):
+    """The oracle's steps with the kernel's storage roundings: bf16 slice weights and X W_U
+    (the bias of U joins the tokens after the weighted sums: a token's weights sum to its
+    weight sum, so sum_I M_IJ (X_I W_U + b_U) / sum_I M_IJ = Z'_J + b_U), bf16 Z^t before the
+    deslice and bf16 X^t."""
+    r = ai.to_bf16_grid
+    M = r(at.slice_weights(X, params["wm"], params["bm"]))
+    U = r(at.affine(X, params["wu"], np.zeros_like(params["bu"])))
+    Z = at.tokens(M, U) + params["bu"]
+    Zt, _ = at.token_attention(Z, params, H, scale)
+    return {"M": M, "Z": Z, "Zt": Zt, "Xt": r(at.deslice(M, r(Zt)))}
+
+
 def _check(params, X, H, scale, got):
     xt, m, z, zt = got
     S = params["wm"].shape[1]
     ref = at.physics_attention(X, params, H, scale)
-    emu = at.physics_attention(X, params, H, scale, rnd=ai.to_bf16_grid)
+    emu = _emulated(X, params, H, scale)
     # slice weights: within one bf16 ulp of the emulated value (2^(e - 7) for a value in
     # [2^e, 2^(e+1))), pad columns exactly zero
     assert np.all(m[:, S:] == 0.0)
@@ -113,7 +126,7 @@ def test_attention_full_cloud_uniform_slices():
     X = ai.random_features(N, C, seed=10)
     xt = _run(P, params, X, 8, 1.0, tokens=False)
     assert np.all(xt == xt[0])
-    ubar = ai.to_bf16_grid(at.affine(X, params["wu"], params["bu"])).mean(axis=0)
+    ubar = ai.to_bf16_grid(at.affine(X, params["wu"], np.zeros_like(params["bu"]))).mean(axis=0) + params["bu"]
     expect = at.affine(ubar[None, :], params["wv"], params["bv"])[0]
     assert rel_l2(xt[0], expect) <= 2e-3
 
