@@ -68,6 +68,16 @@ __device__ __forceinline__ bool vote_any(bool pred, uint32_t id, uint32_t count)
   return out != 0;
 }
 
+constexpr float kLog2e = 1.4426950408889634f;
+
+// 2^x by the hardware approximation (relative error far below the bf16 rounding the slice
+// weights get next); 2^-inf = 0
+__device__ __forceinline__ float fast_exp2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void bulk_wait_read_1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -114,7 +124,10 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
                       const __grid_constant__ CUtensorMap map_m, SliceArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = align1024(smem_raw);
-  const int S = a.S, CS = kC + S;
+  // token columns S .. SP - 1 of W_M are zero and their logit biases -inf, so the padded
+  // slice weights come out exactly 0 without a test on S
+  constexpr int CS = kC + SP;
+  const int S = a.S;
   uint8_t* sw = base;                           // [W_U^T ; W_M^T]: 2 K-regions of CS rows
   uint8_t* sx = sw + 2 * (kC + SP) * 128;       // X: 2 stages x 2 K-regions
   uint8_t* sa = sx + 4 * kRegion;               // M (MN-major A of the slice MMA): 2 regions
@@ -271,18 +284,22 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
       const int j0 = LQ * part;
       float pm = -INFINITY;
 #pragma unroll
-      for (int j = 0; j < LQ; ++j)
-        if (j0 + j < S) {
-          lg[j] += sbias[kC + j0 + j];
-          pm = fmaxf(pm, lg[j]);
-        }
+      for (int j = 0; j < LQ; j += 4) {
+        const float4 b4 = *reinterpret_cast<const float4*>(sbias + kC + j0 + j);
+        lg[j] += b4.x;
+        lg[j + 1] += b4.y;
+        lg[j + 2] += b4.z;
+        lg[j + 3] += b4.w;
+        pm = fmaxf(pm, fmaxf(fmaxf(lg[j], lg[j + 1]), fmaxf(lg[j + 2], lg[j + 3])));
+      }
       xmax[part * kTile + row] = pm;
       named_sync(1 + q, 128);
       const float mx = fmaxf(fmaxf(xmax[row], xmax[kTile + row]), fmaxf(xmax[2 * kTile + row], xmax[3 * kTile + row]));
+      const float mxl = mx * kLog2e;
       float ps = 0.0f;
 #pragma unroll
       for (int j = 0; j < LQ; ++j) {
-        lg[j] = j0 + j < S ? exp2f((lg[j] - mx) * 1.4426950408889634f) : 0.0f;
+        lg[j] = fast_exp2(fmaf(lg[j], kLog2e, -mxl));
         ps += lg[j];
       }
       xsum[part * kTile + row] = ps;
@@ -785,7 +802,7 @@ extern "C" pfem_status pfem_attn_create(int32_t n_channels, int32_t n_tokens, in
     set_error("pfem_attn_create: scale is not finite");
     return PFEM_ERR_INVALID_ARG;
   }
-  const int S = n_tokens, SP = S <= 64 ? 64 : 128, CS = kC + S;
+  const int S = n_tokens, SP = S <= 64 ? 64 : 128, CS = kC + SP;  // W_M padded to SP tokens
   auto* a = new pfem_attn_s();
   a->S = S;
   a->SP = SP;
@@ -802,7 +819,7 @@ extern "C" pfem_status pfem_attn_create(int32_t n_channels, int32_t n_tokens, in
   for (int o = 0; o < S; ++o)
     for (int i = 0; i < kC; ++i) wcat[static_cast<size_t>(kC + o) * kC + i] = __float2bfloat16_rn(w->wm[i * S + o]);
   for (int o = 0; o < kC; ++o) bias[o] = w->bu[o];
-  for (int o = 0; o < S; ++o) bias[kC + o] = w->bm[o];
+  for (int o = 0; o < SP; ++o) bias[kC + o] = o < S ? w->bm[o] : -INFINITY;
   const float* ws[3] = {w->wq, w->wk, w->wv};
   const float* bs[3] = {w->bq, w->bk, w->bv};
   for (int m = 0; m < 3; ++m) {
