@@ -252,13 +252,9 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
     for (int i = 0; i < T; ++i) {
       const int tile = static_cast<int>(blockIdx.x) + i * static_cast<int>(gridDim.x);
       // one thread waits (the others sleep in the vote barrier, which orders them after it):
-      // accumulators ready, slice operands free, the previous M store has read sa
+      // the tile's accumulators are ready
       bool ok = true;
-      if (leader) {
-        ok = mbar_wait(&bar[B_MMA], i & 1, a.err, kWaitNs);
-        ok = ok && mbar_wait(&bar[B_SLICE], (i & 1) ^ 1, a.err, kWaitNs);
-        bulk_wait_read_all();
-      }
+      if (leader) ok = mbar_wait(&bar[B_MMA], i & 1, a.err, kWaitNs);
       if (vote_any(!ok, 5, kSliceEpi)) {
         failed = true;
         break;
@@ -275,10 +271,6 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar[B_TFREE]);
-      // X W_U -> bf16, channels 32 part .. 32 part + 31 of the row of [U | 1]; b_U is added to
-      // the tokens instead (sum_I M_IJ (X_I W_U + b_U) / sum_I M_IJ = Z'_J + b_U)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) st_chunk(sb + (part >> 1) * kRegion, row, (part & 1) * 4 + m, u + 8 * m);
       // M = softmax over the S tokens, the row spread over four threads (zero rows for points
       // past the end); partial maxima and sums combined in quarter order
       const int j0 = LQ * part;
@@ -309,6 +301,21 @@ __global__ void __launch_bounds__(kSliceThreads, 1)
       const float inv = valid ? 1.0f / sum : 0.0f;
 #pragma unroll
       for (int j = 0; j < LQ; ++j) lg[j] *= inv;
+      // the operand buffers are free once the previous tile's slice MMA has read them and its
+      // M store has read sa (the softmax above overlapped that MMA)
+      ok = true;
+      if (leader) {
+        ok = mbar_wait(&bar[B_SLICE], (i & 1) ^ 1, a.err, kWaitNs);
+        bulk_wait_read_all();
+      }
+      if (vote_any(!ok, 5, kSliceEpi)) {
+        failed = true;
+        break;
+      }
+      // X W_U -> bf16, channels 32 part .. 32 part + 31 of the row of [U | 1]; b_U is added to
+      // the tokens instead (sum_I M_IJ (X_I W_U + b_U) / sum_I M_IJ = Z'_J + b_U)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) st_chunk(sb + (part >> 1) * kRegion, row, (part & 1) * 4 + m, u + 8 * m);
       if constexpr (LQ == 32) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) st_chunk(sa + (part >> 1) * kRegion, row, (part & 1) * 4 + m, lg + 8 * m);
