@@ -728,6 +728,7 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
                 raise RuntimeError("served requests did not finish in %.0f s" % timeout_s)
             time.sleep(0.0005)
         makespan = max(v[0] for v in done.values()) - arrive[0]
+        worker = server.stats()
         server.close()
         lat = [done[k][0] - t_sub[k] for k in range(n_run)]
         errs = [float(np.linalg.norm(done[k][3] - urefs[k]) / np.linalg.norm(urefs[k]))
@@ -737,6 +738,7 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
                 "makespan_s": makespan, "converged": sum(done[k][1] == 0 for k in range(n_run)),
                 "latency_ms_p50": 1e3 * _pct(lat, 0.5), "latency_ms_p99": 1e3 * _pct(lat, 0.99),
                 "pcg_iterations_total": int(sum(done[k][2]["iterations"] for k in range(n_run))),
+                "worker": worker,
                 "vs_reference_rel_l2": {"requests": len(errs), "max": max(errs) if errs else None,
                                         "median": _pct(errs, 0.5) if errs else None,
                                         "reference": "%s solve of each warm request to %g" % (ref_precision, ref_tol)}}

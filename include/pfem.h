@@ -375,6 +375,13 @@ pfem_status pfem_serve_submit(pfem_server_t server, const pfem_mesh_desc* desc, 
 pfem_status pfem_serve_poll(pfem_server_t server, uint64_t ticket, double* u_out_host,
                             pfem_solve_info* info);
 
+/* Worker-thread accounting since creation, out[0..7]: seconds spent waiting for the device
+ * after each chunk of shared steps, admitting requests (uploads, solve set-up), rebuilding
+ * the device tables and capturing the chunk graph, and running the per-request state
+ * machine; then the counts of chunks, table rebuilds and admitted requests; out[7] = 0.
+ * Values are read without stopping the worker. */
+pfem_status pfem_serve_stats(pfem_server_t server, double* out);
+
 /* Waits (at most timeout_s) until every submitted request has finished; TIMEOUT otherwise. */
 pfem_status pfem_serve_drain(pfem_server_t server, double timeout_s);
 

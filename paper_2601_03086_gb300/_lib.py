@@ -127,6 +127,7 @@ SIGNATURES = {
                                       C.POINTER(C.c_uint64)]),
     "pfem_serve_poll": (C.c_int32, [C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(SolveInfo)]),
     "pfem_serve_drain": (C.c_int32, [C.c_void_p, C.c_double]),
+    "pfem_serve_stats": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double)]),
     "pfem_serve_destroy": (None, [C.c_void_p]),
     "pfem_attn_create": (C.c_int32, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.POINTER(AttnWeights), C.c_void_p,
                                      C.POINTER(C.c_void_p)]),

@@ -496,6 +496,14 @@ class Server:
     def drain(self, timeout_s=600.0):
         check(lib().pfem_serve_drain(self.handle, float(timeout_s)))
 
+    def stats(self):
+        """Worker-thread accounting (pfem_serve_stats): seconds waiting for the device after
+        chunks, admitting, rebuilding tables, running the state machine; counts."""
+        out = (C.c_double * 8)()
+        check(lib().pfem_serve_stats(self.handle, out))
+        keys = ("wait_s", "admit_s", "tables_s", "advance_s", "chunks", "rebuilds", "admitted")
+        return {k: (int(out[i]) if i >= 4 else out[i]) for i, k in enumerate(keys)}
+
     def close(self):
         if getattr(self, "handle", None):
             lib().pfem_serve_destroy(self.handle)
@@ -518,6 +526,10 @@ def pfem_serve_submit(server, problem, u0=None, tol=1e-8, solve="linear", n_load
 
 def pfem_serve_poll(server, ticket):
     return server.poll(ticket)
+
+
+def pfem_serve_stats(server):
+    return server.stats()
 
 
 def pfem_serve_drain(server, timeout_s=600.0):

@@ -174,6 +174,9 @@ struct pfem_server_s {
   cudaGraphExec_t chunk_exec = nullptr;
   int64_t chunk_kernels = 0;       // kernels per replay of the chunk graph
   bool graph_failed = false;       // capture unavailable: plain launches
+  // worker-thread wall time by activity (s) and counts, for pfem_serve_stats
+  std::atomic<double> t_wait{0.0}, t_admit{0.0}, t_tables{0.0}, t_advance{0.0};
+  std::atomic<int64_t> n_chunks{0}, n_rebuilds{0}, n_admitted{0};
 };
 
 namespace pfem {
@@ -686,6 +689,7 @@ void worker_loop(pfem_server_s* S) {
       }
     }
     for (Request* R : rejected) finish(S, R, R->plan_status);
+    const auto t_a0 = std::chrono::steady_clock::now();
     for (Request* R : admitted) {
       pfem_status st = admit(S, R);
       if (st == PFEM_OK) st = start_solve(R, S->stream);
@@ -701,8 +705,12 @@ void worker_loop(pfem_server_s* S) {
       S->active.push_back(R);
       S->dirty = true;
     }
+    const auto t_a1 = std::chrono::steady_clock::now();
+    S->t_admit = S->t_admit + std::chrono::duration<double>(t_a1 - t_a0).count();
+    S->n_admitted += (int64_t)admitted.size();
     if (S->active.empty()) continue;
     if (S->dirty) {
+      S->n_rebuilds++;
       if (rebuild_tables(S) != PFEM_OK) {
         for (Request* R : S->active) finish(S, R, PFEM_ERR_CUDA);
         S->active.clear();
@@ -711,6 +719,8 @@ void worker_loop(pfem_server_s* S) {
       }
       if (!S->graph_failed && capture_chunk(S) != PFEM_OK) S->graph_failed = true;  // plain launches from now on
     }
+    const auto t_c0 = std::chrono::steady_clock::now();
+    S->t_tables = S->t_tables + std::chrono::duration<double>(t_c0 - t_a1).count();
     // ---- a chunk of shared steps, then one read-back of every solve's scalars
     const int na = (int)S->active.size();
     bool launched = false;
@@ -719,7 +729,11 @@ void worker_loop(pfem_server_s* S) {
       if (launched) g_kernel_launches += S->chunk_kernels;
     }
     if (!launched) enqueue_chunk(S, S->stream);
-    if (cudaStreamSynchronize(S->stream) != cudaSuccess) {
+    S->n_chunks++;
+    const bool synced = cudaStreamSynchronize(S->stream) == cudaSuccess;
+    const auto t_c1 = std::chrono::steady_clock::now();
+    S->t_wait = S->t_wait + std::chrono::duration<double>(t_c1 - t_c0).count();
+    if (!synced) {
       for (Request* R : S->active) finish(S, R, PFEM_ERR_CUDA);
       S->active.clear();
       continue;
@@ -731,6 +745,7 @@ void worker_loop(pfem_server_s* S) {
       else S->dirty = true;
     }
     S->active.swap(still);
+    S->t_advance = S->t_advance + std::chrono::duration<double>(std::chrono::steady_clock::now() - t_c1).count();
   }
 }
 
@@ -877,6 +892,22 @@ pfem_status pfem_serve_poll(pfem_server_t S, uint64_t ticket, double* u_out_host
   if (st != PFEM_OK) set_error("request %llu finished with status %d", (unsigned long long)ticket, (int)st);
   delete R;
   return st;
+}
+
+pfem_status pfem_serve_stats(pfem_server_t S, double* out) {
+  if (!S || !out) {
+    set_error("pfem_serve_stats: NULL argument");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  out[0] = S->t_wait;
+  out[1] = S->t_admit;
+  out[2] = S->t_tables;
+  out[3] = S->t_advance;
+  out[4] = (double)S->n_chunks;
+  out[5] = (double)S->n_rebuilds;
+  out[6] = (double)S->n_admitted;
+  out[7] = 0.0;
+  return PFEM_OK;
 }
 
 pfem_status pfem_serve_drain(pfem_server_t S, double timeout_s) {
