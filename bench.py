@@ -681,6 +681,7 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
            "tets_total": int(sum(r["n_tets"] for r in reqs)), "warm_start_prep_s": t_prep,
            "linear": sum(r["kind"] == "linear" for r in reqs), "warm": sum(u is not None for u in u0s),
            "plain_loop_sample": {"every": plain_every, "requests": len(sample)}}
+    loop_info = {}
     for mode_name, mode in (("plain_loop", MODES["plain"]), ("graph_loop", MODES["graph"])):
         P.pfem_set_solver_mode(mode)
         torch.cuda.synchronize()
@@ -692,6 +693,8 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
             b = time.perf_counter()
             _, info = solve_one(m, r, u0)
             m.close()
+            loop_info.setdefault(k, {})[mode_name] = (info["iterations"], info["newton_iterations"],
+                                                     time.perf_counter() - b)
             lat.append(time.perf_counter() - a)
             plan_s += b - a
             total += time.perf_counter() - a
@@ -702,6 +705,8 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
                           "plan_upload_s": plan_all, "solves_per_s_excluding_planning": n_req / (wall - plan_all),
                           "solve_ms_p50": 1e3 * _pct(lat, 0.5), "solve_ms_p99": 1e3 * _pct(lat, 0.99)}
     P.pfem_set_solver_mode(MODES["graph"])
+
+    served_iters = []
 
     def served_run(rate_factor, n_run=None):
         n_run = n_req if n_run is None else min(n_run, n_req)
@@ -730,6 +735,7 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
         makespan = max(v[0] for v in done.values()) - arrive[0]
         worker = server.stats()
         server.close()
+        served_iters.append({k: (done[k][2]["iterations"], done[k][2]["newton_iterations"]) for k in range(n_run)})
         lat = [done[k][0] - t_sub[k] for k in range(n_run)]
         errs = [float(np.linalg.norm(done[k][3] - urefs[k]) / np.linalg.norm(urefs[k]))
                 for k in range(n_run) if urefs[k] is not None and done[k][1] == 0]
@@ -744,6 +750,11 @@ def _serving(P, pi, torch, np, n_req=400, rate_factors=(20.0,), hi=50_000, plain
                                         "reference": "%s solve of each warm request to %g" % (ref_precision, ref_tol)}}
 
     runs = [served_run(*(f if isinstance(f, tuple) else (f,))) for f in rate_factors]
+    # per sampled request: size, kind, start, PCG / Newton iterations and solve seconds of the
+    # graph loop against the PCG / Newton iterations of the first served run
+    out["sampled_requests"] = [
+        {"request": k, "tets": int(reqs[k]["n_tets"]), "kind": reqs[k]["kind"], "warm": u0s[k] is not None,
+         "graph_loop": loop_info[k].get("graph_loop"), "served": served_iters[0].get(k)} for k in sample]
     out["served"] = runs[0]
     if len(runs) > 1:
         out["served_runs"] = runs
