@@ -529,20 +529,29 @@ __global__ void __launch_bounds__(256) attn_qkv_kernel(const float* zsum, const 
                                                        const float* bqkv, int S, float* z, float* qkv) {
   __shared__ float sz[32][kC + 1];
   __shared__ float sw[kC][33];
+  __shared__ float sden[32];
   const int m = blockIdx.x >> 2, c0 = (blockIdx.x & 3) * 32, r0 = blockIdx.y * 32;
-  for (int e = threadIdx.x; e < 32 * kC; e += blockDim.x) {
-    const int j = e / kC, c = e % kC, row = r0 + j;
-    float v = 0.0f;
-    if (row < S) {
-      const float w = zsum[row * kPartPitch + kC];
-      v = w > 0.0f ? zsum[row * kPartPitch + c] / w + bias_u[c] : 0.0f;
-      if (blockIdx.x == 0) z[row * kC + c] = v;
-    }
-    sz[j][c] = v;
+  if (threadIdx.x < 32) sden[threadIdx.x] = r0 + threadIdx.x < S ? zsum[(r0 + threadIdx.x) * kPartPitch + kC] : 0.0f;
+  // every load of the staging issued before the first use (fixed trip counts, 256 threads)
+  constexpr int kIt = 32 * kC / 256;
+  float zv[kIt], wv[kIt];
+#pragma unroll
+  for (int k = 0; k < kIt; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    const int j = e / kC, c = e % kC;
+    zv[k] = r0 + j < S ? zsum[(r0 + j) * kPartPitch + c] : 0.0f;
+    wv[k] = wqkv[static_cast<int64_t>(m) * kC * kC + (e >> 5) * kC + c0 + (e & 31)];
   }
-  for (int e = threadIdx.x; e < kC * 32; e += blockDim.x) {
-    const int c = e >> 5, t = e & 31;
-    sw[c][t] = wqkv[static_cast<int64_t>(m) * kC * kC + c * kC + c0 + t];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kIt; ++k) {
+    const int e = threadIdx.x + 256 * k;
+    const int j = e / kC, c = e % kC, row = r0 + j;
+    const float w = sden[j];
+    const float v = w > 0.0f ? zv[k] / w + bias_u[c] : 0.0f;
+    if (blockIdx.x == 0 && row < S) z[row * kC + c] = v;
+    sz[j][c] = v;
+    sw[e >> 5][e & 31] = wv[k];
   }
   __syncthreads();
   const int t = threadIdx.x & 31, jb = threadIdx.x >> 5;
@@ -572,10 +581,21 @@ __global__ void __launch_bounds__(128) attn_heads_kernel(const float* qkv, int S
   float* sk = sh;          // [S][D]
   float* sv = sh + S * D;  // [S][D]
   const int h = blockIdx.x, a = blockIdx.y * 32 + (threadIdx.x >> 2), part = threadIdx.x & 3;
-  for (int e = threadIdx.x; e < S * D; e += blockDim.x) {
-    const int b = e / D, t = e % D;
-    sk[e] = qkv[(static_cast<int64_t>(S) + b) * kC + h * D + t];
-    sv[e] = qkv[(2 * static_cast<int64_t>(S) + b) * kC + h * D + t];
+  // staging with every load issued first: S * D <= 128 D elements over 128 threads
+  float kv[D], vv[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const int e = threadIdx.x + 128 * k, b = e / D, t = e % D;
+    kv[k] = e < S * D ? qkv[(static_cast<int64_t>(S) + b) * kC + h * D + t] : 0.0f;
+    vv[k] = e < S * D ? qkv[(2 * static_cast<int64_t>(S) + b) * kC + h * D + t] : 0.0f;
+  }
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const int e = threadIdx.x + 128 * k;
+    if (e < S * D) {
+      sk[e] = kv[k];
+      sv[e] = vv[k];
+    }
   }
   __syncthreads();
   float qa[D], o[D];
