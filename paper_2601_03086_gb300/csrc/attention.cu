@@ -507,9 +507,20 @@ __global__ void __launch_bounds__(256) attn_reduce_kernel(const float* partial, 
   const int j = blockIdx.x, cb = blockIdx.y;
   const int cl = threadIdx.x & 31, g0 = threadIdx.x >> 5;
   const int c = 32 * cb + cl;
+  // partials g0, g0 + 8, ... in that order; loads issued kBatch at a time before their sums
+  constexpr int kBatch = 10;
   float acc = 0.0f;
   if (c <= kC)
-    for (int g = g0; g < G; g += 8) acc += partial[(static_cast<int64_t>(g) * S + j) * kPartPitch + c];
+    for (int g1 = g0; g1 < G; g1 += 8 * kBatch) {
+      float v[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int g = g1 + 8 * k;
+        v[k] = g < G ? partial[(static_cast<int64_t>(g) * S + j) * kPartPitch + c] : 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) acc += v[k];
+    }
   red[g0][cl] = acc;
   __syncthreads();
   if (g0 == 0 && c <= kC) {
