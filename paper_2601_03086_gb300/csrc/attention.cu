@@ -16,9 +16,10 @@
 // columns S..S_pad-1 zero).  Each 128-point tile moves through shared memory in 64-column
 // regions with the 128-byte swizzle, the layout TMA writes and the MMA descriptors read.
 // Operands the epilogue produces (M and [U | 1] of the slice MMA) are written row by row,
-// one point per thread, as MN-major operands, so no transpose is needed.
+// four threads per point (a quarter of the columns each), as MN-major operands, so no
+// transpose is needed.
 //
-// Precision: bf16 operands, FP32 accumulation; U, M, Z^t and X^t are stored in bf16, the
+// Precision: bf16 operands, FP32 accumulation; X W_U, M, Z^t and X^t are stored in bf16, the
 // tokens, Q/K/V and the attention in FP32.  Deterministic: fixed tile-to-CTA assignment and
 // fixed-order reductions, no atomics.
 //
@@ -104,7 +105,7 @@ __device__ __forceinline__ uint8_t* align1024(uint8_t* p) {
 struct SliceArgs {
   int64_t n_points;
   int32_t n_tiles, S;
-  const float* bias;  // [C + S]: b_U then b_M
+  const float* bias;  // [C + S_pad]: b_U, then b_M with -inf for the padded tokens
   float* partial;     // [gridDim.x][S][kPartPitch]
   int* err;
 };
@@ -671,8 +672,8 @@ struct pfem_attn_s {
   float scale = 1.0f;
   cudaStream_t stream = nullptr;
   int n_sm = 0;
-  __nv_bfloat16* wcat = nullptr;  // [C + S][C]: rows = output channels of W_U then W_M (K-major)
-  float* bias = nullptr;          // [C + S]
+  __nv_bfloat16* wcat = nullptr;  // [C + S_pad][C]: rows = output channels of W_U, W_M, zero pad (K-major)
+  float* bias = nullptr;          // [C + S_pad]: b_U, b_M, -inf pad
   float* wqkv = nullptr;          // [3][C][C] (in, out)
   float* bqkv = nullptr;          // [3][C]
   float* partial = nullptr;       // [n_sm][S][kPartPitch]
