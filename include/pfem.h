@@ -444,6 +444,23 @@ void pfem_attn_destroy(pfem_attn_t attn);
 pfem_status pfem_attn_set_timing(pfem_attn_t attn, int32_t on);
 pfem_status pfem_attn_kernel_ms(pfem_attn_t attn, double* ms);
 
+/* ---- bounds-checked build ------------------------------------------------------------
+ * libpfem_checked.so is the same library compiled with PFEM_CHECKED: the element-tile
+ * kernels check every global node index and halo-partial range they gather or scatter
+ * through; an index out of range is replaced by 0 (a valid address) and flagged instead of
+ * dereferenced. */
+
+/* Checked build: synchronise the device, then *word = OR of the flags raised since the last
+ * call (bit 0: node index out of range, bit 1: partial range out of range, bit 31: the flag
+ * could not be read), and clear them. Regular build: *word = 0, UNSUPPORTED. */
+pfem_status pfem_check_status(uint32_t* word);
+
+/* Checked build, for tests of the checks: overwrite the global node id of tile-node record
+ * local_node (0 <= local_node < stats.n_local_nodes) with node_id (< 2^28, any value,
+ * in range or not). Synchronises the mesh's stream. Regular build: UNSUPPORTED, nothing
+ * changed. */
+pfem_status pfem_debug_set_node_id(pfem_mesh_t mesh, int64_t local_node, int64_t node_id);
+
 /* ---- misc ------------------------------------------------------------------------- */
 
 const char* pfem_last_error(void);

@@ -137,6 +137,8 @@ SIGNATURES = {
     "pfem_attn_destroy": (None, [C.c_void_p]),
     "pfem_attn_set_timing": (C.c_int32, [C.c_void_p, C.c_int32]),
     "pfem_attn_kernel_ms": (C.c_int32, [C.c_void_p, C.POINTER(C.c_double)]),
+    "pfem_check_status": (C.c_int32, [C.POINTER(C.c_uint32)]),
+    "pfem_debug_set_node_id": (C.c_int32, [C.c_void_p, C.c_int64, C.c_int64]),
     "pfem_last_error": (C.c_char_p, []),
     "pfem_version": (C.c_char_p, []),
 }
@@ -150,18 +152,24 @@ class PfemError(RuntimeError):
         self.status = status
 
 
+def load(path):
+    """Open a build of the library at `path` (libpfem.so or the bounds-checked
+    libpfem_checked.so) with every signature declared."""
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built; run paper_2601_03086_gb300.build.build() first" % os.path.basename(path))
+    h = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(h, name)
+        fn.restype = res
+        fn.argtypes = args
+    return h
+
+
 def lib():
     """Load libpfem.so (raises if it has not been built: there is no fallback path)."""
     global _LIB
     if _LIB is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError("libpfem.so is not built; run paper_2601_03086_gb300.build.build() first")
-        h = C.CDLL(LIB_PATH)
-        for name, (res, args) in SIGNATURES.items():
-            fn = getattr(h, name)
-            fn.restype = res
-            fn.argtypes = args
-        _LIB = h
+        _LIB = load(LIB_PATH)
     return _LIB
 
 

@@ -15,6 +15,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpfem.so")
+LIB_PLAIN = LIB
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3", "-I" + INCLUDE]
@@ -44,8 +45,14 @@ def _compile(src, obj, extra):
     return res.stderr
 
 
-def build(force=False, verbose=False, ptxas_info=False, jobs=None):
-    """Compile and link libpfem.so; returns its path."""
+LIB_CHECKED = os.path.join(PKG, "libpfem_checked.so")
+
+
+def build(force=False, verbose=False, ptxas_info=False, jobs=None, checked=False):
+    """Compile and link libpfem.so (checked=True: libpfem_checked.so, the bounds-checked
+    build compiled with -DPFEM_CHECKED into its own object folder); returns its path."""
+    BUILD = os.path.join(PKG, "_build_checked" if checked else "_build")
+    LIB = LIB_CHECKED if checked else LIB_PLAIN
     os.makedirs(BUILD, exist_ok=True)
     hdr_mtime = max((os.path.getmtime(h) for h in _headers()), default=0.0)
     todo = []
@@ -55,7 +62,7 @@ def build(force=False, verbose=False, ptxas_info=False, jobs=None):
         objs.append(obj)
         if force or not os.path.exists(obj) or os.path.getmtime(obj) < max(os.path.getmtime(src), hdr_mtime):
             todo.append((src, obj))
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DPFEM_CHECKED"] if checked else [])
     logs = {}
     if todo:
         with cf.ThreadPoolExecutor(max_workers=jobs or min(len(todo), os.cpu_count() or 4)) as ex:

@@ -31,6 +31,18 @@ pfem_status upload(void* base, size_t off, const std::vector<T>& v, cudaStream_t
 
 }  // namespace
 
+// Readers of the bad-index words of the checked kernels' modules (bounds-checked build only;
+// registered at load time, before any other thread runs).
+static std::vector<unsigned (*)()>& check_words() {
+  static std::vector<unsigned (*)()> v;
+  return v;
+}
+
+bool register_check_word(unsigned (*read_and_clear)()) {
+  check_words().push_back(read_and_clear);
+  return true;
+}
+
 pfem_status check_mesh(pfem_mesh_t m) {
   if (!m) {
     set_error("null mesh");
@@ -46,7 +58,54 @@ using namespace pfem;
 extern "C" {
 
 const char* pfem_last_error(void) { return last_error_cstr(); }
+#ifdef PFEM_CHECKED
+const char* pfem_version(void) { return "pfem-gb300 0.1 (sm_103a, bounds-checked)"; }
+#else
 const char* pfem_version(void) { return "pfem-gb300 0.1 (sm_103a)"; }
+#endif
+
+pfem_status pfem_check_status(uint32_t* word) {
+  if (!word) {
+    set_error("pfem_check_status: word is NULL");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  *word = 0;
+#ifdef PFEM_CHECKED
+  PFEM_CUDA(cudaDeviceSynchronize());
+  for (auto f : check_words()) *word |= f();
+  return PFEM_OK;
+#else
+  set_error("not a bounds-checked build (libpfem_checked.so has the checks)");
+  return PFEM_ERR_UNSUPPORTED;
+#endif
+}
+
+pfem_status pfem_debug_set_node_id(pfem_mesh_t m, int64_t local_node, int64_t node_id) {
+#ifdef PFEM_CHECKED
+  pfem_status st = check_mesh(m);
+  if (st) return st;
+  if (local_node < 0 || local_node >= m->stats.n_local_nodes || node_id < 0 || node_id > (int64_t)kInfoIdMask) {
+    set_error("pfem_debug_set_node_id: index out of range");
+    return PFEM_ERR_INVALID_ARG;
+  }
+  float4* rec = const_cast<float4*>(m->plan.lnode_f) + local_node;
+  float4 r;
+  PFEM_CUDA(cudaStreamSynchronize(m->stream));
+  PFEM_CUDA(cudaMemcpy(&r, rec, sizeof(r), cudaMemcpyDeviceToHost));
+  unsigned info;
+  std::memcpy(&info, &r.w, sizeof(info));
+  info = (info & ~kInfoIdMask) | ((unsigned)node_id & kInfoIdMask);
+  std::memcpy(&r.w, &info, sizeof(info));
+  PFEM_CUDA(cudaMemcpy(rec, &r, sizeof(r), cudaMemcpyHostToDevice));
+  return PFEM_OK;
+#else
+  (void)m;
+  (void)local_node;
+  (void)node_id;
+  set_error("pfem_debug_set_node_id exists only in the bounds-checked build");
+  return PFEM_ERR_UNSUPPORTED;
+#endif
+}
 
 pfem_status pfem_mesh_create(const pfem_mesh_desc* desc, void* cuda_stream, pfem_mesh_t* out) {
   if (!out) {

@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) multi_kernel(DevPlan P, Multi
     // ---- the pair's field on the tile's nodes (0 on prescribed DOFs)
     for (int l = threadIdx.x; l < nl; l += blockDim.x) {
       const unsigned info = (unsigned)sinfo[l];
-      const int64_t gid = (int64_t)(info & kInfoIdMask);
+      const int64_t gid = checked_node((int64_t)(info & kInfoIdMask), P.n_nodes);
       const unsigned mask = info >> kInfoIdBits;
       F2 w[3] = {};
 #pragma unroll
@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) multi_kernel(DevPlan P, Multi
       }
       if (l < ncomp) {
         const unsigned info = (unsigned)sinfo[l];
-        const int64_t gid = (int64_t)(info & kInfoIdMask);
+        const int64_t gid = checked_node((int64_t)(info & kInfoIdMask), P.n_nodes);
         const unsigned mask = info >> kInfoIdBits;
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) multi_halo_kernel(DevPlan P, MultiArgs M)
     for (int i = 0; i < DIM; ++i) acc[i] = add2(acc[i], d[i]);
   }
   const unsigned info = (unsigned)rec.z;
-  const int64_t gid = (int64_t)(info & kInfoIdMask);
+  const int64_t gid = checked_node((int64_t)(info & kInfoIdMask), P.n_nodes);
   const unsigned mask = info >> kInfoIdBits;
   const VT* v = static_cast<const VT*>(M.v);
   VT* y = static_cast<VT*>(M.y);

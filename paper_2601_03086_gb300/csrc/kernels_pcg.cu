@@ -227,7 +227,7 @@ __device__ __forceinline__ void resident_stage_static(const DevPlan& P, const do
     soff[l] = (int)P.slot_off[lbeg + l];
     hslot[l] = l >= ncomp ? P.halo_rec[pbeg + l - ncomp].x : -1;
     if constexpr (KIND == K_NH) {
-      const int64_t gid = (int64_t)((unsigned)__float_as_int(rf.w) & kInfoIdMask);
+      const int64_t gid = checked_node((int64_t)((unsigned)__float_as_int(rf.w) & kInfoIdMask), P.n_nodes);
       float w[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 0; i < DIM; ++i) w[i] = (float)u[gid * DIM + i];
@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(kTileThreads, KIND == K_LIN ? 4 : 3)
       double* p_new = odd ? sA.p[0] : sA.p[1];
       for (int l = threadIdx.x, nl = s_nl, ncomp = s_ncomp; l < nl; l += blockDim.x) {
         const unsigned info = (unsigned)sinfo[l];
-        const int64_t gid = (int64_t)(info & kInfoIdMask);
+        const int64_t gid = checked_node((int64_t)(info & kInfoIdMask), P.n_nodes);
         const unsigned mask = info >> kInfoIdBits;
         float w[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kTileThreads, KIND == K_LIN ? 4 : 3)
         e_acc += pap_node<DIM, float>(sv + 4 * l, acc);  // as node_pass
         if (l < ncomp) {
           const unsigned info = (unsigned)sinfo[l];
-          const int64_t gid = (int64_t)(info & kInfoIdMask);
+          const int64_t gid = checked_node((int64_t)(info & kInfoIdMask), P.n_nodes);
 #pragma unroll
           for (int i = 0; i < DIM; ++i)
             sA.q[gid * DIM + i] = ((info >> (kInfoIdBits + i)) & 1u) ? 0.0 : (double)acc[i];

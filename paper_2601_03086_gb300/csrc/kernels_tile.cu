@@ -227,14 +227,18 @@ __global__ void __launch_bounds__(256) halo_finish_kernel(DevPlan P, OpArgs A, i
   const CT sc = A.out_scale ? CT(*static_cast<const VT*>(A.out_scale)) : CT(1);
   const int4 rec = P.halo_node[h];
   CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
-  for (int k = rec.x; k < rec.x + rec.y; ++k) {
+  const int n_seq = checked_range(rec.x, rec.y, P.n_partials) ? rec.y : 0;
+  for (int k = rec.x; k < rec.x + n_seq; ++k) {
     CT t[4];
-    ld4(part + 4 * (size_t)P.halo_seq[k], t);
+    int64_t q = P.halo_seq[k];
+    if (!checked_range(q, 1, P.n_partials)) q = 0;
+    ld4(part + 4 * (size_t)q, t);
 #pragma unroll
     for (int i = 0; i < DIM; ++i) sum[i] += t[i];
   }
   const unsigned info = (unsigned)rec.z;
-  final_write<DIM, OUT, VT, CT>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, sum, sc);
+  final_write<DIM, OUT, VT, CT>(P, A, checked_node((int64_t)(info & kInfoIdMask), P.n_nodes), info >> kInfoIdBits,
+                                sum, sc);
 }
 
 template <int DIM, int OUT, typename VT, typename CT>

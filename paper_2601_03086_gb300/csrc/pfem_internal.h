@@ -69,6 +69,10 @@ extern thread_local int64_t g_kernel_launches;
 #define PFEM_COUNT_LAUNCH() (++::pfem::g_kernel_launches)
 
 void set_error(const char* fmt, ...);
+
+// Bounds-checked build: each translation unit with checked kernels registers a host function
+// that reads and clears its device word of bad-index flags (see checked.cuh).
+bool register_check_word(unsigned (*read_and_clear)());
 pfem_status cuda_fail(cudaError_t e, const char* what);
 
 #define PFEM_CUDA(call)                                         \

@@ -24,6 +24,7 @@
 #include <cuda/atomic>
 #include <type_traits>
 
+#include "checked.cuh"
 #include "element.cuh"
 #include "pcg_state.cuh"
 #include "pfem_internal.h"
@@ -365,6 +366,7 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
   for (int l = threadIdx.x; l < nl; l += blockDim.x) {
     int slot_i = pbeg + l - ncomp;  // deferred: tile order, no load on the way
     if (l >= ncomp && !defer) slot_i = P.halo_rec[slot_i].x;  // issued before the slot sums
+    if (l >= ncomp && !checked_range(slot_i, 1, P.n_partials)) slot_i = 0;
     const int b = soff[l], e = soff[l + 1];
     CT acc[4] = {CT(0), CT(0), CT(0), CT(0)};
     for (int k = b; k < e; ++k) {
@@ -376,7 +378,8 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
     if constexpr (PCG) *e_pap += pap_node<DIM, CT>(reinterpret_cast<const CT*>(smem + L.v) + 4 * l, acc);
     if (l < ncomp) {
       const unsigned info = (unsigned)sinfo[l];
-      final_write<DIM, OUT, VT, CT, PCG>(P, A, (int64_t)(info & kInfoIdMask), info >> kInfoIdBits, acc, sc);
+      final_write<DIM, OUT, VT, CT, PCG>(P, A, checked_node((int64_t)(info & kInfoIdMask), P.n_nodes),
+                                         info >> kInfoIdBits, acc, sc);
       continue;
     }
     // halo node: publish this tile's partial in the node's contiguous range
@@ -391,7 +394,7 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
   __syncthreads();
   for (int l = ncomp + threadIdx.x; l < nl; l += blockDim.x) {
     const int4 rec = P.halo_rec[pbeg + l - ncomp];
-    if (atomicAdd(count + rec.y, 1) == rec.z - 1) {
+    if (checked_range(rec.y, rec.z, P.n_partials) && atomicAdd(count + rec.y, 1) == rec.z - 1) {
       __threadfence();
       CT sum[4] = {CT(0), CT(0), CT(0), CT(0)};
       for (int k = rec.y; k < rec.y + rec.z; ++k) {
@@ -401,7 +404,7 @@ __device__ __forceinline__ void node_pass(const DevPlan& P, const OpArgs& A, uns
         for (int i = 0; i < DIM; ++i) sum[i] += t[i];
       }
       const unsigned hinfo = (unsigned)rec.w;
-      const int64_t hgid = (int64_t)(hinfo & kInfoIdMask);
+      const int64_t hgid = checked_node((int64_t)(hinfo & kInfoIdMask), P.n_nodes);
       if constexpr (PCG) {  // the node's new direction, as every tile staged it
 #pragma unroll
         for (int i = 0; i < DIM; ++i) {
@@ -524,7 +527,7 @@ __device__ __forceinline__ void process_tile(const DevPlan& P, const OpArgs& A, 
         for (int i = 0; i < 3; ++i) wu[q][i] = wv[q][i] = CT(0);
         if (ls[q] >= nl) continue;
         const unsigned info = (unsigned)__float_as_int(rf[q].w);
-        const int64_t gid = (int64_t)(info & kInfoIdMask);
+        const int64_t gid = checked_node((int64_t)(info & kInfoIdMask), P.n_nodes);
         const unsigned mask = info >> kInfoIdBits;
         if constexpr (NEED_U) {
 #pragma unroll
