@@ -36,6 +36,21 @@ def test_header_symbols_exported(libpfem):
         assert hasattr(libpfem, n), n
 
 
+def test_checked_build_exports_header_and_reports_itself():
+    """The bounds-checked twin exports the same C ABI; its version string says what it is,
+    and the regular build answers pfem_check_status with UNSUPPORTED (no GPU call needed)."""
+    from paper_2601_03086_gb300 import _lib, build
+
+    checked = _lib.load(build.build(checked=True))
+    for n in _declared_symbols():
+        assert hasattr(checked, n), n
+    assert b"bounds-checked" in checked.pfem_version()
+    assert b"bounds-checked" not in _lib.lib().pfem_version()
+    w = ctypes.c_uint32(7)
+    assert _lib.STATUS[_lib.lib().pfem_check_status(ctypes.byref(w))] == "PFEM_ERR_UNSUPPORTED"
+    assert w.value == 0
+
+
 def test_python_binding_covers_header():
     from paper_2601_03086_gb300 import _lib
 
